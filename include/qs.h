@@ -1,0 +1,162 @@
+/*
+ * qs.h -- C-ABI of the GB300 (sm_103a) hybrid Quicksort library (libqs.so).
+ *
+ * The operations are those of Bramas, "A Novel Hybrid Quicksort Algorithm
+ * Vectorized using AVX-512 on Intel Skylake" (arXiv 1704.08579):
+ *   - partition an array around a pivot          (Section III-B, Algorithm 2)
+ *   - sort an array in place: partition until the parts are small, then sort
+ *     the parts with a branch-free Bitonic network (Sections III-A and III-C,
+ *     Algorithm 3; small-array sort Section III-A, Algorithms 1 and 2)
+ *   - the same for key/value pairs held in two separate arrays (Section III-D)
+ * for three element kinds: int32 keys ("i32"), IEEE double keys ("f64"), and
+ * int32 keys carrying int32 values ("kv").
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named d_* are CUDA device pointers on the current device.  The
+ *     caller owns them; the library never frees or keeps them after the call.
+ *     Keys must be aligned to their element size (4 or 8 bytes), values to 4.
+ *   - n is an element count, 0 <= n <= 2^38.  n == 0 (and n == 1 for sorts)
+ *     succeeds without touching memory.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     issued on it, and every entry point returns only after that work has
+ *     finished (it synchronises the stream once, to read the result/status).
+ *   - The library owns one workspace per device (scratch arrays of n keys and
+ *     n values, a task queue, look-back words); it grows on demand or by
+ *     qs_reserve(), and is guarded by a mutex, so concurrent calls on one
+ *     device are serialised.
+ *   - f64 keys must contain no NaN and no -0.0 (not checked).
+ *   - Errors: a negative qs_status; qs_last_error() then describes it.  A
+ *     device-side failure (a bounded wait that ran out, a capacity overflow)
+ *     leaves the array contents unspecified but a permutation is NOT
+ *     guaranteed; the library stays usable.
+ */
+#ifndef QS_H_
+#define QS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *qs_stream_t; /* == cudaStream_t */
+
+typedef enum {
+    QS_OK = 0,
+    QS_ERR_INVALID_ARG = -1, /* bad pointer, negative or too large n, bad kind/option */
+    QS_ERR_ALIGN = -2,       /* pointer not aligned to its element size */
+    QS_ERR_OOM = -3,         /* workspace allocation failed */
+    QS_ERR_CUDA = -4,        /* a CUDA runtime call failed */
+    QS_ERR_TIMEOUT = -5,     /* a device-side bounded wait ran out */
+    QS_ERR_CAPACITY = -6,    /* task / look-back / leaf capacity exceeded on the device */
+    QS_ERR_INTERNAL = -7     /* recursion deeper than the supported limit */
+} qs_status;
+
+typedef enum { QS_KIND_I32 = 0, QS_KIND_F64 = 1, QS_KIND_KV = 2 } qs_kind;
+
+/*
+ * Partition (Section III-B): reorders d_keys[0..n) so that every key strictly
+ * below `pivot` comes first and every key at-or-above it comes last, and
+ * returns the split index = the number of keys below the pivot (the paper's
+ * returned left_w), in [0, n].  The order inside each side is fixed: the lower
+ * side keeps input order, the upper side holds its keys in reverse input
+ * order.  For kv, d_vals[i] moves with d_keys[i].
+ * The kernel partitions out of place into the workspace scratch (one read and
+ * one write of each element) and copies the result back into d_keys/d_vals.
+ * Returns a negative qs_status on error.
+ */
+int64_t qs_partition_i32(int32_t *d_keys, int64_t n, int32_t pivot, qs_stream_t stream);
+int64_t qs_partition_f64(double *d_keys, int64_t n, double pivot, qs_stream_t stream);
+int64_t qs_partition_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, int32_t pivot,
+                        qs_stream_t stream);
+
+/*
+ * Sort in place into non-decreasing key order (Section III-C, Algorithm 3):
+ * device-wide partitions around sampled-median pivots, driven by one
+ * persistent kernel and a device work queue, until every part holds at most
+ * a leaf-sized number of keys; a Bitonic network (Section III-A) then sorts
+ * each part into d_keys.  Keys equal to a pivot that can no longer be split
+ * are finished as a block.  For kv the values follow their keys; the order of
+ * values among equal keys is unspecified (the method is not stable).
+ * Returns QS_OK or a negative qs_status.
+ */
+int qs_sort_i32(int32_t *d_keys, int64_t n, qs_stream_t stream);
+int qs_sort_f64(double *d_keys, int64_t n, qs_stream_t stream);
+int qs_sort_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, qs_stream_t stream);
+
+/*
+ * Host-buffer sorts: h_keys (and h_vals) are HOST pointers (pinned memory is
+ * fastest).  The library copies them into a device staging area owned by the
+ * workspace, sorts there with the qs_sort_* path, and copies the result back,
+ * all on `stream`.  Same return convention as qs_sort_*.
+ */
+int qs_sort_host_i32(int32_t *h_keys, int64_t n, qs_stream_t stream);
+int qs_sort_host_f64(double *h_keys, int64_t n, qs_stream_t stream);
+int qs_sort_host_kv(int32_t *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream);
+
+/*
+ * Grows the current device's workspace so that calls of `kind` with up to n
+ * elements allocate nothing.  Returns QS_OK or a negative qs_status.
+ */
+int qs_reserve(int64_t n, int kind);
+
+/* Frees the current device's workspace (a later call re-creates it). */
+void qs_release(void);
+
+/* Text of the last error raised on this host thread ("" if none). */
+const char *qs_last_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int qs_version(void);
+
+/*
+ * Counters of the last qs_sort_* / qs_partition_* call on this host thread.
+ * The byte figures let a caller compute the HBM traffic the schedule moves:
+ * every element of a device-wide partition is read once and written once,
+ * so are leaf-sorted and copied elements.
+ */
+typedef struct {
+    int64_t n;              /* elements in the call */
+    int64_t kind;           /* qs_kind */
+    int64_t part_tasks;     /* device-wide partition passes run */
+    int64_t part_keys;      /* sum of their lengths */
+    int64_t leaf_parts;     /* parts sorted by the Bitonic leaf kernel */
+    int64_t leaf_keys;      /* sum of their lengths */
+    int64_t copy_keys;      /* finished equal-key elements copied back from scratch */
+    int64_t max_depth;      /* deepest partition level reached */
+    int64_t lookback_words; /* look-back words used */
+    int64_t grid_driver;    /* CTAs of the persistent partition kernel */
+    int64_t grid_leaf;      /* CTAs of the leaf kernel */
+    double ms_driver;       /* device time of the partition kernel (profiling on) */
+    double ms_leaf;         /* device time of the leaf kernel (profiling on) */
+    double ms_copy;         /* device time of the partition copy-back (profiling on) */
+    double ms_total;        /* device time of the whole call (profiling on) */
+} qs_stats;
+
+int qs_get_stats(qs_stats *out);
+
+/*
+ * Options (process-wide).  Returns QS_OK or QS_ERR_INVALID_ARG.
+ *   QS_OPT_PROFILE       0/1: record CUDA events around each kernel of a
+ *                        call, on the call's stream (fills ms_* in qs_stats).
+ *   QS_OPT_WAIT_LIMIT_NS limit of every device-side wait (default 2e9 ns);
+ *                        a wait that runs out ends the kernel with
+ *                        QS_ERR_TIMEOUT instead of hanging.
+ *   QS_OPT_TASK_CAP      if > 0, caps the device task table (to exercise
+ *                        QS_ERR_CAPACITY); 0 = size from n.
+ *   QS_OPT_DRIVER_CTAS   if > 0, number of CTAs of the persistent kernels;
+ *                        0 = all resident CTAs.
+ */
+enum {
+    QS_OPT_PROFILE = 1,
+    QS_OPT_WAIT_LIMIT_NS = 2,
+    QS_OPT_TASK_CAP = 3,
+    QS_OPT_DRIVER_CTAS = 4
+};
+int qs_set_option(int option, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QS_H_ */

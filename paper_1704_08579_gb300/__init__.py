@@ -1,0 +1,210 @@
+"""Python binding of libqs.so, the GB300 (sm_103a) hybrid Quicksort library.
+
+Argument marshalling only: every step of partitioning and sorting runs in the
+library's CUDA kernels.  The names follow the C-ABI in ``include/qs.h``:
+
+    partition(keys, pivot, values=None)  -> split index   (qs_partition_*)
+    sort(keys, values=None)                               (qs_sort_*)
+    sort_host(keys, values=None)                          (qs_sort_host_*)
+
+``keys``/``values`` are contiguous CUDA tensors (int32 or float64 keys, int32
+values) for ``partition``/``sort`` and contiguous numpy arrays for
+``sort_host``.  Work is issued on the current torch CUDA stream (or the one
+passed).  There is no CPU fallback: if the library has not been built, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libqs.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "qs.h")
+
+QS_OK = 0
+STATUS = {
+    -1: "QS_ERR_INVALID_ARG", -2: "QS_ERR_ALIGN", -3: "QS_ERR_OOM", -4: "QS_ERR_CUDA",
+    -5: "QS_ERR_TIMEOUT", -6: "QS_ERR_CAPACITY", -7: "QS_ERR_INTERNAL",
+}
+KIND = {"i32": 0, "f64": 1, "kv": 2}
+OPTION = {"profile": 1, "wait_limit_ns": 2, "task_cap": 3, "driver_ctas": 4}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class QSError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "QS_ERR"), code, message))
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "n", "kind", "part_tasks", "part_keys", "leaf_parts", "leaf_keys", "copy_keys", "max_depth",
+        "lookback_words", "grid_driver", "grid_leaf")] + [
+        (name, ctypes.c_double) for name in ("ms_driver", "ms_leaf", "ms_copy", "ms_total")]
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/qs.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qs_[a-z0-9_]+)\s*\(", text)))
+
+
+def load() -> ctypes.CDLL:
+    """Loads libqs.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libqs.so is not built (%s); run paper_1704_08579_gb300.build.build()" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        i64, i32, f64, vp, ci = ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_void_p, ctypes.c_int
+        sig = {
+            "qs_partition_i32": ([vp, i64, i32, vp], i64),
+            "qs_partition_f64": ([vp, i64, f64, vp], i64),
+            "qs_partition_kv": ([vp, vp, i64, i32, vp], i64),
+            "qs_sort_i32": ([vp, i64, vp], ci),
+            "qs_sort_f64": ([vp, i64, vp], ci),
+            "qs_sort_kv": ([vp, vp, i64, vp], ci),
+            "qs_sort_host_i32": ([vp, i64, vp], ci),
+            "qs_sort_host_f64": ([vp, i64, vp], ci),
+            "qs_sort_host_kv": ([vp, vp, i64, vp], ci),
+            "qs_reserve": ([i64, ci], ci),
+            "qs_release": ([], None),
+            "qs_last_error": ([], ctypes.c_char_p),
+            "qs_version": ([], ci),
+            "qs_get_stats": ([ctypes.POINTER(Stats)], ci),
+            "qs_set_option": ([ci, i64], ci),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def last_error() -> str:
+    return load().qs_last_error().decode()
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise QSError(rc, last_error())
+    return rc
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _kind_of(keys, values) -> str:
+    import torch
+
+    if values is not None:
+        if keys.dtype != torch.int32 or values.dtype != torch.int32:
+            raise TypeError("key/value sorting takes int32 keys and int32 values")
+        return "kv"
+    if keys.dtype == torch.int32:
+        return "i32"
+    if keys.dtype == torch.float64:
+        return "f64"
+    raise TypeError("keys must be int32 or float64, got %s" % keys.dtype)
+
+
+def _check_tensor(t, name):
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+def partition(keys, pivot, values=None, stream=None) -> int:
+    """qs_partition_*: reorders keys (and values) around pivot; returns the split index."""
+    lib = load()
+    kind = _kind_of(keys, values)
+    _check_tensor(keys, "keys")
+    s = _stream_handle(stream)
+    n = keys.numel()
+    if kind == "kv":
+        _check_tensor(values, "values")
+        if values.numel() != n:
+            raise ValueError("keys and values differ in length")
+        return _check(lib.qs_partition_kv(keys.data_ptr(), values.data_ptr(), n, int(pivot), s))
+    if kind == "i32":
+        return _check(lib.qs_partition_i32(keys.data_ptr(), n, int(pivot), s))
+    return _check(lib.qs_partition_f64(keys.data_ptr(), n, float(pivot), s))
+
+
+def sort(keys, values=None, stream=None) -> None:
+    """qs_sort_*: sorts keys (and values with them) in place."""
+    lib = load()
+    kind = _kind_of(keys, values)
+    _check_tensor(keys, "keys")
+    s = _stream_handle(stream)
+    n = keys.numel()
+    if kind == "kv":
+        _check_tensor(values, "values")
+        if values.numel() != n:
+            raise ValueError("keys and values differ in length")
+        _check(lib.qs_sort_kv(keys.data_ptr(), values.data_ptr(), n, s))
+    elif kind == "i32":
+        _check(lib.qs_sort_i32(keys.data_ptr(), n, s))
+    else:
+        _check(lib.qs_sort_f64(keys.data_ptr(), n, s))
+
+
+def sort_host(keys, values=None, stream=None) -> None:
+    """qs_sort_host_*: sorts host (numpy) arrays in place through the GPU."""
+    import numpy as np
+
+    lib = load()
+    s = _stream_handle(stream)
+    if not keys.flags.c_contiguous:
+        raise ValueError("keys must be C-contiguous")
+    n = keys.size
+    p = ctypes.c_void_p(keys.ctypes.data)
+    if values is not None:
+        if keys.dtype != np.int32 or values.dtype != np.int32 or values.size != n or not values.flags.c_contiguous:
+            raise ValueError("key/value host sort takes contiguous int32 arrays of equal length")
+        _check(lib.qs_sort_host_kv(p, ctypes.c_void_p(values.ctypes.data), n, s))
+    elif keys.dtype == np.int32:
+        _check(lib.qs_sort_host_i32(p, n, s))
+    elif keys.dtype == np.float64:
+        _check(lib.qs_sort_host_f64(p, n, s))
+    else:
+        raise TypeError(keys.dtype)
+
+
+def reserve(n: int, kind: str) -> None:
+    _check(load().qs_reserve(int(n), KIND[kind]))
+
+
+def release() -> None:
+    load().qs_release()
+
+
+def set_option(name: str, value: int) -> None:
+    _check(load().qs_set_option(OPTION[name], int(value)))
+
+
+def stats() -> dict:
+    st = Stats()
+    _check(load().qs_get_stats(ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in Stats._fields_}
+
+
+def version() -> int:
+    return load().qs_version()

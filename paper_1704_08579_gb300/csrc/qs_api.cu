@@ -1,0 +1,503 @@
+// C-ABI of libqs.so: argument checks, the per-device workspace, and dispatch
+// to the per-kind launchers.  Every entry point is declared and documented in
+// include/qs.h.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/qs.h"
+#include "qs_internal.h"
+
+namespace qs {
+namespace {
+
+thread_local std::string t_error;
+thread_local qs_stats t_stats;
+
+std::atomic<int> g_profile{0};
+std::atomic<int64_t> g_wait_limit_ns{2000000000ll};
+std::atomic<int64_t> g_task_cap{0};
+std::atomic<int64_t> g_driver_ctas{0};
+
+constexpr int64_t kMaxN = 1ll << 38;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(QS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct Workspace {
+    std::mutex mu;
+    bool init = false;
+    int sms = 0;
+    int occ[3][2] = {};
+    void *scratch_k = nullptr, *scratch_v = nullptr;
+    size_t scratch_k_bytes = 0, scratch_v_bytes = 0;
+    void *stage_k = nullptr, *stage_v = nullptr;
+    size_t stage_k_bytes = 0, stage_v_bytes = 0;
+    Task *tasks = nullptr;
+    int32_t *queue = nullptr;
+    int64_t task_cap = 0;
+    unsigned long long *pool = nullptr;
+    int64_t pool_cap = 0;
+    Leaf *leaves = nullptr;
+    int64_t leaf_cap = 0;
+    Ctrl *ctrl = nullptr;
+    Ctrl *h_ctrl = nullptr;
+    bool dirty = true;  // look-back words / queue slots must be cleared before use
+    cudaEvent_t ev[6] = {};
+};
+
+constexpr int kMaxDevices = 64;
+Workspace *g_ws[kMaxDevices] = {};
+std::mutex g_ws_mu;
+
+Workspace *workspace_for(int dev)
+{
+    std::lock_guard<std::mutex> g(g_ws_mu);
+    if (!g_ws[dev]) g_ws[dev] = new Workspace();
+    return g_ws[dev];
+}
+
+KernelLimits limits_of(int kind)
+{
+    return kind == QS_KIND_I32 ? limits_i32() : kind == QS_KIND_F64 ? limits_f64() : limits_kv();
+}
+
+int occupancy_of(int kind, int which, int *bps)
+{
+    return kind == QS_KIND_I32 ? occupancy_i32(which, bps)
+           : kind == QS_KIND_F64 ? occupancy_f64(which, bps)
+                                 : occupancy_kv(which, bps);
+}
+
+// Grows a device buffer to at least `bytes`; contents are not preserved.
+int grow(void **p, size_t *have, size_t bytes, const char *what)
+{
+    if (*have >= bytes && *p) return QS_OK;
+    if (*p) {
+        cudaError_t e = cudaFree(*p);
+        *p = nullptr;
+        *have = 0;
+        if (e != cudaSuccess) return cuda_fail(e, what);
+    }
+    cudaError_t e = cudaMalloc(p, bytes < 256 ? 256 : bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(QS_ERR_OOM, "cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+    }
+    *have = bytes < 256 ? 256 : bytes;
+    return QS_OK;
+}
+
+int ws_init(Workspace &w)
+{
+    if (w.init) return QS_OK;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    for (int k = 0; k < 3; ++k)
+        for (int which = 0; which < 2; ++which) {
+            e = static_cast<cudaError_t>(occupancy_of(k, which, &w.occ[k][which]));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+            if (w.occ[k][which] < 1) return fail(QS_ERR_INTERNAL, "kernel cannot be resident (kind %d)", k);
+        }
+    e = cudaMalloc(&w.ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) return fail(QS_ERR_OOM, "cudaMalloc(ctrl): %s", cudaGetErrorString(e));
+    e = cudaMallocHost(&w.h_ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) return fail(QS_ERR_OOM, "cudaMallocHost(ctrl): %s", cudaGetErrorString(e));
+    for (auto &ev : w.ev) {
+        e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    }
+    w.init = true;
+    return QS_OK;
+}
+
+struct Needs {
+    size_t key_bytes, val_bytes;
+    int64_t task_cap, pool_cap, leaf_cap;
+};
+
+Needs needs_for(int64_t n, int kind)
+{
+    const KernelLimits l = limits_of(kind);
+    Needs r;
+    r.key_bytes = static_cast<size_t>(n) * (kind == QS_KIND_F64 ? 8 : 4);
+    r.val_bytes = kind == QS_KIND_KV ? static_cast<size_t>(n) * 4 : 0;
+    const int64_t cap_override = g_task_cap.load();
+    r.task_cap = cap_override > 0 ? cap_override : 8 * (n / l.leaf_max) + 1024;
+    r.pool_cap = 64 * (n / l.tile + 1) + 2 * r.task_cap + 4096;
+    r.leaf_cap = 4 * r.task_cap + n / kCopyChunk + 1024;
+    return r;
+}
+
+int ws_ensure(Workspace &w, int64_t n, int kind)
+{
+    int rc = ws_init(w);
+    if (rc) return rc;
+    const Needs nd = needs_for(n, kind);
+    if ((rc = grow(&w.scratch_k, &w.scratch_k_bytes, nd.key_bytes, "scratch keys"))) return rc;
+    if (nd.val_bytes && (rc = grow(&w.scratch_v, &w.scratch_v_bytes, nd.val_bytes, "scratch values"))) return rc;
+    const bool override_cap = g_task_cap.load() > 0;
+    if (w.task_cap < nd.task_cap || (override_cap && w.task_cap != nd.task_cap)) {
+        // Task table and queue are sized together (one queue slot per task).
+        if (w.tasks) cudaFree(w.tasks);
+        if (w.queue) cudaFree(w.queue);
+        w.tasks = nullptr;
+        w.queue = nullptr;
+        w.task_cap = 0;
+        size_t have_t = 0, have_q = 0;
+        if ((rc = grow(reinterpret_cast<void **>(&w.tasks), &have_t, nd.task_cap * sizeof(Task), "tasks"))) return rc;
+        if ((rc = grow(reinterpret_cast<void **>(&w.queue), &have_q, nd.task_cap * sizeof(int32_t), "queue"))) return rc;
+        w.task_cap = nd.task_cap;
+        w.dirty = true;
+    }
+    if (w.pool_cap < nd.pool_cap) {
+        size_t have = w.pool ? static_cast<size_t>(w.pool_cap) * 8 : 0;
+        if ((rc = grow(reinterpret_cast<void **>(&w.pool), &have, nd.pool_cap * 8, "look-back words"))) return rc;
+        w.pool_cap = nd.pool_cap;
+        w.dirty = true;
+    }
+    if (w.leaf_cap < nd.leaf_cap) {
+        size_t have = w.leaves ? static_cast<size_t>(w.leaf_cap) * sizeof(Leaf) : 0;
+        if ((rc = grow(reinterpret_cast<void **>(&w.leaves), &have, nd.leaf_cap * sizeof(Leaf), "leaf list"))) return rc;
+        w.leaf_cap = nd.leaf_cap;
+    }
+    return QS_OK;
+}
+
+void ws_free(Workspace &w)
+{
+    if (!w.init) return;
+    cudaDeviceSynchronize();
+    void *bufs[] = {w.scratch_k, w.scratch_v, w.stage_k, w.stage_v, w.tasks, w.queue, w.pool, w.leaves, w.ctrl};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (w.h_ctrl) cudaFreeHost(w.h_ctrl);
+    for (auto &ev : w.ev)
+        if (ev) cudaEventDestroy(ev);
+    w.scratch_k = w.scratch_v = w.stage_k = w.stage_v = nullptr;
+    w.scratch_k_bytes = w.scratch_v_bytes = w.stage_k_bytes = w.stage_v_bytes = 0;
+    w.tasks = nullptr;
+    w.queue = nullptr;
+    w.pool = nullptr;
+    w.leaves = nullptr;
+    w.ctrl = nullptr;
+    w.h_ctrl = nullptr;
+    w.task_cap = w.pool_cap = w.leaf_cap = 0;
+    for (auto &ev : w.ev) ev = nullptr;
+    w.dirty = true;
+    w.init = false;
+}
+
+template <class K>
+int phase_of(const void *p)
+{
+    return static_cast<int>((reinterpret_cast<uintptr_t>(p) / sizeof(K)) % (16 / sizeof(K)));
+}
+
+const char *status_text(int s)
+{
+    switch (s) {
+    case QS_ERR_TIMEOUT: return "a device-side wait ran out (QS_OPT_WAIT_LIMIT_NS)";
+    case QS_ERR_CAPACITY: return "device task/look-back/leaf capacity exceeded";
+    case QS_ERR_INTERNAL: return "recursion deeper than the supported limit";
+    default: return "device error";
+    }
+}
+
+// Runs one sort (partition_only = 0) or partition (1) of kind `kind` on the
+// current device.  keys/vals are device pointers.
+template <class K>
+int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, int partition_only,
+            qs_stream_t stream)
+{
+    t_error.clear();
+    std::memset(&t_stats, 0, sizeof(t_stats));
+    t_stats.n = n;
+    t_stats.kind = kind;
+    if (n < 0 || n > kMaxN) return fail(QS_ERR_INVALID_ARG, "n = %lld out of range [0, 2^38]", (long long)n);
+    if (n == 0 || (n == 1 && !partition_only)) {
+        if (partition_only) return 0;
+        return QS_OK;
+    }
+    if (!keys) return fail(QS_ERR_INVALID_ARG, "null key pointer");
+    if (kind == QS_KIND_KV && !vals) return fail(QS_ERR_INVALID_ARG, "null value pointer");
+    if (reinterpret_cast<uintptr_t>(keys) % sizeof(K)) return fail(QS_ERR_ALIGN, "keys not aligned to %zu bytes", sizeof(K));
+    if (vals && reinterpret_cast<uintptr_t>(vals) % 4) return fail(QS_ERR_ALIGN, "values not aligned to 4 bytes");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(QS_ERR_INVALID_ARG, "device %d out of range", dev);
+    Workspace &w = *workspace_for(dev);
+    std::lock_guard<std::mutex> guard(w.mu);
+    int rc = ws_ensure(w, n, kind);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (w.dirty) {
+        if ((e = cudaMemsetAsync(w.pool, 0, static_cast<size_t>(w.pool_cap) * 8, s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync");
+        if ((e = cudaMemsetAsync(w.queue, 0, static_cast<size_t>(w.task_cap) * 4, s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync");
+        w.dirty = false;
+    }
+    const KernelLimits lim = limits_of(kind);
+    Args<K, int32_t> a;
+    std::memset(&a, 0, sizeof(a));
+    a.keys[0] = keys;
+    a.keys[1] = static_cast<K *>(w.scratch_k);
+    a.vals[0] = vals;
+    a.vals[1] = kind == QS_KIND_KV ? static_cast<int32_t *>(w.scratch_v) : nullptr;
+    for (int b = 0; b < 2; ++b) {
+        a.key_phase[b] = phase_of<K>(a.keys[b]);
+        a.val_vec[b] = a.vals[b] ? (phase_of<int32_t>(a.vals[b]) == a.key_phase[b]) : 1;
+    }
+    a.n = n;
+    a.tasks = w.tasks;
+    a.queue = w.queue;
+    a.pool = w.pool;
+    a.leaves = w.leaves;
+    a.ctrl = w.ctrl;
+    a.task_cap = w.task_cap;
+    a.pool_cap = w.pool_cap;
+    a.leaf_cap = w.leaf_cap;
+    a.leaf_max = lim.leaf_max;
+    a.small_max = lim.small_max;
+    a.wait_limit_ns = static_cast<uint64_t>(g_wait_limit_ns.load());
+    a.pivot_bits = pivot_bits;
+    a.partition_only = partition_only;
+
+    LaunchCfg cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.stream = s;
+    const int64_t ctas = g_driver_ctas.load();
+    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][0];
+    cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];
+    cfg.profile = g_profile.load();
+    for (int i = 0; i < 6; ++i) cfg.ev[i] = w.ev[i];
+
+    int le = 0;
+    if constexpr (sizeof(K) == 8)
+        le = launch_f64(a, cfg);
+    else
+        le = kind == QS_KIND_I32 ? launch_i32(a, cfg) : launch_kv(a, cfg);
+    if (le != cudaSuccess) return cuda_fail(static_cast<cudaError_t>(le), "kernel launch");
+    if ((e = cudaMemcpyAsync(w.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(status)");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const Ctrl &c = *w.h_ctrl;
+    t_stats.part_tasks = static_cast<int64_t>(c.part_tasks);
+    t_stats.part_keys = static_cast<int64_t>(c.part_keys);
+    t_stats.leaf_parts = static_cast<int64_t>(c.leaf_parts);
+    t_stats.leaf_keys = static_cast<int64_t>(c.leaf_keys);
+    t_stats.copy_keys = static_cast<int64_t>(c.copy_keys);
+    t_stats.max_depth = static_cast<int64_t>(c.max_depth);
+    t_stats.lookback_words = static_cast<int64_t>(c.pool_cursor);
+    t_stats.grid_driver = cfg.grid_driver;
+    t_stats.grid_leaf = cfg.grid_leaf;
+    if (c.status != 0) {
+        w.dirty = true;
+        return fail(c.status, "%s (code %d, detail %d)", status_text(c.status), c.status, c.info);
+    }
+    if (partition_only) {
+        // The split is known; move the partitioned data back into the caller's arrays.
+        if (cfg.profile) cudaEventRecord(w.ev[4], s);
+        if ((e = cudaMemcpyAsync(keys, w.scratch_k, static_cast<size_t>(n) * sizeof(K), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(copy-back)");
+        if (kind == QS_KIND_KV &&
+            (e = cudaMemcpyAsync(vals, w.scratch_v, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(copy-back)");
+        if (cfg.profile) cudaEventRecord(w.ev[5], s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
+    if (cfg.profile) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) t_stats.ms_driver = ms;
+        if (!partition_only && cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]) == cudaSuccess) t_stats.ms_leaf = ms;
+        if (partition_only && cudaEventElapsedTime(&ms, w.ev[4], w.ev[5]) == cudaSuccess) t_stats.ms_copy = ms;
+        if (cudaEventElapsedTime(&ms, w.ev[0], partition_only ? w.ev[5] : w.ev[3]) == cudaSuccess) t_stats.ms_total = ms;
+    }
+    return partition_only ? static_cast<int64_t>(c.lt_result) : QS_OK;
+}
+
+template <class K>
+int run_host(int kind, K *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream)
+{
+    t_error.clear();
+    if (n < 0 || n > kMaxN) return fail(QS_ERR_INVALID_ARG, "n = %lld out of range [0, 2^38]", (long long)n);
+    if (n < 2) return QS_OK;
+    if (!h_keys || (kind == QS_KIND_KV && !h_vals)) return fail(QS_ERR_INVALID_ARG, "null host pointer");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(QS_ERR_INVALID_ARG, "device %d out of range", dev);
+    Workspace &w = *workspace_for(dev);
+    K *dk = nullptr;
+    int32_t *dv = nullptr;
+    {
+        std::lock_guard<std::mutex> guard(w.mu);
+        int rc = ws_init(w);
+        if (rc) return rc;
+        if ((rc = grow(&w.stage_k, &w.stage_k_bytes, static_cast<size_t>(n) * sizeof(K), "staging keys"))) return rc;
+        if (kind == QS_KIND_KV && (rc = grow(&w.stage_v, &w.stage_v_bytes, static_cast<size_t>(n) * 4, "staging values")))
+            return rc;
+        dk = static_cast<K *>(w.stage_k);
+        dv = static_cast<int32_t *>(w.stage_v);
+    }
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((e = cudaMemcpyAsync(dk, h_keys, static_cast<size_t>(n) * sizeof(K), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(H2D)");
+    if (kind == QS_KIND_KV &&
+        (e = cudaMemcpyAsync(dv, h_vals, static_cast<size_t>(n) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(H2D)");
+    const int64_t rc = run<K>(kind, dk, kind == QS_KIND_KV ? dv : nullptr, n, 0, 0, stream);
+    if (rc) return static_cast<int>(rc);
+    if ((e = cudaMemcpyAsync(h_keys, dk, static_cast<size_t>(n) * sizeof(K), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    if (kind == QS_KIND_KV &&
+        (e = cudaMemcpyAsync(h_vals, dv, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return QS_OK;
+}
+
+uint64_t bits_i32(int32_t k) { return static_cast<uint64_t>(static_cast<int64_t>(k)); }
+uint64_t bits_f64(double k)
+{
+    uint64_t b;
+    std::memcpy(&b, &k, 8);
+    return b;
+}
+
+}  // namespace
+}  // namespace qs
+
+using namespace qs;
+
+extern "C" {
+
+int64_t qs_partition_i32(int32_t *d_keys, int64_t n, int32_t pivot, qs_stream_t stream)
+{
+    return run<int32_t>(QS_KIND_I32, d_keys, nullptr, n, bits_i32(pivot), 1, stream);
+}
+
+int64_t qs_partition_f64(double *d_keys, int64_t n, double pivot, qs_stream_t stream)
+{
+    return run<double>(QS_KIND_F64, d_keys, nullptr, n, bits_f64(pivot), 1, stream);
+}
+
+int64_t qs_partition_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, int32_t pivot, qs_stream_t stream)
+{
+    return run<int32_t>(QS_KIND_KV, d_keys, d_vals, n, bits_i32(pivot), 1, stream);
+}
+
+int qs_sort_i32(int32_t *d_keys, int64_t n, qs_stream_t stream)
+{
+    return static_cast<int>(run<int32_t>(QS_KIND_I32, d_keys, nullptr, n, 0, 0, stream));
+}
+
+int qs_sort_f64(double *d_keys, int64_t n, qs_stream_t stream)
+{
+    return static_cast<int>(run<double>(QS_KIND_F64, d_keys, nullptr, n, 0, 0, stream));
+}
+
+int qs_sort_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, qs_stream_t stream)
+{
+    return static_cast<int>(run<int32_t>(QS_KIND_KV, d_keys, d_vals, n, 0, 0, stream));
+}
+
+int qs_sort_host_i32(int32_t *h_keys, int64_t n, qs_stream_t stream)
+{
+    return run_host<int32_t>(QS_KIND_I32, h_keys, nullptr, n, stream);
+}
+
+int qs_sort_host_f64(double *h_keys, int64_t n, qs_stream_t stream)
+{
+    return run_host<double>(QS_KIND_F64, h_keys, nullptr, n, stream);
+}
+
+int qs_sort_host_kv(int32_t *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream)
+{
+    return run_host<int32_t>(QS_KIND_KV, h_keys, h_vals, n, stream);
+}
+
+int qs_reserve(int64_t n, int kind)
+{
+    t_error.clear();
+    if (n < 0 || n > kMaxN) return fail(QS_ERR_INVALID_ARG, "n out of range");
+    if (kind < QS_KIND_I32 || kind > QS_KIND_KV) return fail(QS_ERR_INVALID_ARG, "bad kind %d", kind);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(QS_ERR_INVALID_ARG, "device %d out of range", dev);
+    Workspace &w = *workspace_for(dev);
+    std::lock_guard<std::mutex> guard(w.mu);
+    return ws_ensure(w, n, kind);
+}
+
+void qs_release(void)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return;
+    Workspace &w = *workspace_for(dev);
+    std::lock_guard<std::mutex> guard(w.mu);
+    ws_free(w);
+}
+
+const char *qs_last_error(void) { return t_error.c_str(); }
+
+int qs_version(void) { return 100; }
+
+int qs_get_stats(qs_stats *out)
+{
+    if (!out) return QS_ERR_INVALID_ARG;
+    *out = t_stats;
+    return QS_OK;
+}
+
+int qs_set_option(int option, int64_t value)
+{
+    switch (option) {
+    case QS_OPT_PROFILE:
+        g_profile = value ? 1 : 0;
+        return QS_OK;
+    case QS_OPT_WAIT_LIMIT_NS:
+        if (value < 0) return QS_ERR_INVALID_ARG;
+        g_wait_limit_ns = value;
+        return QS_OK;
+    case QS_OPT_TASK_CAP:
+        if (value < 0) return QS_ERR_INVALID_ARG;
+        g_task_cap = value;
+        return QS_OK;
+    case QS_OPT_DRIVER_CTAS:
+        if (value < 0 || value > (1 << 20)) return QS_ERR_INVALID_ARG;
+        g_driver_ctas = value;
+        return QS_OK;
+    default:
+        return QS_ERR_INVALID_ARG;
+    }
+}
+
+}  // extern "C"

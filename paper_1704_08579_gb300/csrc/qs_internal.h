@@ -1,0 +1,123 @@
+// Internal declarations shared by the CUDA translation units of libqs.so.
+//
+// Device-resident state of one sort (all in the per-device workspace):
+//   Task   -- one device-wide partition of a range [off, off+len) of buffer
+//             `src` (0 = caller's array, 1 = scratch) around `pivot`; split
+//             into tiles that any CTA of the persistent kernel may claim.
+//   queue  -- FIFO of task ids (+1; 0 = slot reserved but not yet written).
+//   pool   -- look-back words, one per tile of every task (Merrill & Garland
+//             single-pass scan with decoupled look-back): 2 flag bits
+//             (aggregate available / inclusive prefix available) + 62-bit
+//             count of keys sent to the lower side.
+//   leaves -- parts left for the Bitonic kernel.  "Large" entries fill the
+//             array from the front (one CTA each), "small" ones from the back
+//             (one warp each).
+//   Ctrl   -- queue cursors, allocation cursors, pending-task count, status
+//             word and statistics.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace qs {
+
+constexpr int kThreads = 256;            // threads per CTA in every kernel
+constexpr int kWarps = kThreads / 32;
+
+constexpr uint64_t kFlagAggregate = 1ull << 62;
+constexpr uint64_t kFlagPrefix = 2ull << 62;
+constexpr uint64_t kCountMask = (1ull << 62) - 1;
+
+constexpr int kMaxDepth = 250;           // deeper recursion => QS_ERR_INTERNAL
+constexpr int64_t kCopyChunk = 1 << 15;  // finished equal-key runs are copied in chunks
+
+enum TaskMode : int32_t { kModeLess = 0, kModeLessEqual = 1 };
+
+struct alignas(16) Task {
+    int64_t off;        // first element of the range
+    int64_t len;        // elements in the range
+    int64_t w0;         // first element of tile 0 (16-byte aligned address, <= off)
+    int64_t pool;       // index of tile 0's look-back word
+    uint64_t pivot;     // key bits (int32 sign-extended, or double bits)
+    int32_t ntiles;
+    int32_t src;        // buffer holding the range: 0 caller, 1 scratch
+    int32_t mode;       // TaskMode
+    int32_t depth;
+    unsigned long long next_tile;   // tile claim counter
+    unsigned long long tiles_done;  // completion counter
+    unsigned long long eq;          // keys equal to the pivot
+    unsigned long long lt_total;    // keys sent to the lower side (written by the last tile)
+};
+
+struct alignas(16) Leaf {
+    int64_t off;
+    int32_t len;
+    int32_t flags;  // bit 0: range lives in scratch; bit 1: finished (copy only)
+};
+constexpr int kLeafScratch = 1;
+constexpr int kLeafFinal = 2;
+
+struct alignas(128) Ctrl {
+    unsigned long long q_head, q_tail;
+    unsigned long long n_tasks, pool_cursor;
+    long long pending;  // device-wide partition tasks created and not finished
+    unsigned long long n_large, n_small;
+    unsigned long long claim_large, claim_small;
+    int status, info;
+    // statistics
+    unsigned long long part_tasks, part_keys, leaf_parts, leaf_keys, copy_keys, max_depth;
+    unsigned long long lt_result;  // split index of a partition-only call
+    unsigned long long exited;     // CTAs of the persistent kernel that left cleanly
+};
+
+// Arguments of the device kernels (passed by value).
+template <class K, class V>
+struct Args {
+    K *keys[2];   // [0] caller array, [1] scratch
+    V *vals[2];
+    int key_phase[2];  // (address / sizeof(K)) % (16 / sizeof(K)) of each key buffer
+    int val_vec[2];    // value buffer shares the key buffer's 16-byte phase
+    int64_t n;
+    Task *tasks;
+    int32_t *queue;
+    unsigned long long *pool;
+    Leaf *leaves;
+    Ctrl *ctrl;
+    int64_t task_cap, pool_cap, leaf_cap;
+    int64_t leaf_max;   // parts up to this size go to the Bitonic kernel
+    int64_t small_max;  // parts up to this size are sorted by one warp
+    uint64_t wait_limit_ns;
+    uint64_t pivot_bits;  // partition-only: the caller's pivot
+    int partition_only;
+};
+
+// Launch description computed by the host and consumed by the per-kind launchers.
+struct LaunchCfg {
+    void *stream;
+    int grid_driver;
+    int grid_leaf;
+    int profile;
+    void *ev[6];  // cudaEvent_t when profiling
+};
+
+struct KernelLimits {
+    int64_t leaf_max, small_max, tile;
+    size_t driver_smem, leaf_smem;
+};
+
+// Per-kind entry points implemented in qs_kind_{i32,f64,kv}.cu.  They enqueue
+// setup + persistent partition kernel + leaf kernel (sort) or setup +
+// persistent kernel (partition only) on cfg.stream and return a cudaError_t.
+int launch_i32(const Args<int32_t, int32_t> &a, LaunchCfg &cfg);
+int launch_f64(const Args<double, int32_t> &a, LaunchCfg &cfg);
+int launch_kv(const Args<int32_t, int32_t> &a, LaunchCfg &cfg);
+KernelLimits limits_i32();
+KernelLimits limits_f64();
+KernelLimits limits_kv();
+// Resident CTAs per SM of the persistent kernel (which = 0) or the leaf
+// kernel (which = 1) of each kind.
+int occupancy_i32(int which, int *blocks_per_sm);
+int occupancy_f64(int which, int *blocks_per_sm);
+int occupancy_kv(int which, int *blocks_per_sm);
+
+}  // namespace qs

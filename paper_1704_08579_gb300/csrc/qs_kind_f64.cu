@@ -1,0 +1,15 @@
+// Kernel instantiation and launcher for the "f64" element kind.
+#include "qs_kernels.cuh"
+
+namespace qs {
+
+namespace {
+using Tr = Traits<double, false, 4, 4096, 512>;
+using L = Launcher<Tr, 4, 2>;
+}  // namespace
+
+int launch_f64(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg) { return L::launch(a, cfg); }
+KernelLimits limits_f64() { return L::limits(); }
+int occupancy_f64(int which, int *bps) { return L::occ(which, bps); }
+
+}  // namespace qs

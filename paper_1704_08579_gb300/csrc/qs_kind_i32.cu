@@ -1,0 +1,15 @@
+// Kernel instantiation and launcher for the "i32" element kind.
+#include "qs_kernels.cuh"
+
+namespace qs {
+
+namespace {
+using Tr = Traits<int32_t, false, 4, 8192, 512>;
+using L = Launcher<Tr, 4, 2>;
+}  // namespace
+
+int launch_i32(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg) { return L::launch(a, cfg); }
+KernelLimits limits_i32() { return L::limits(); }
+int occupancy_i32(int which, int *bps) { return L::occ(which, bps); }
+
+}  // namespace qs

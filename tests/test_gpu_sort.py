@@ -1,0 +1,178 @@
+"""GPU parity of qs_sort_{i32,f64,kv} against the oracle (Appendix A / Sections
+III-A..III-D).  Keys must be bit-identical to the oracle's; for key/value
+pairs each run of equal keys must hold the same multiset of values.
+
+Sizes cover the single-warp leaf (<= 512), the CTA leaf (<= 8192 i32,
+<= 4096 f64/kv), several device-wide partition levels, ragged tails,
+duplicate-heavy and all-equal inputs, extreme keys and unaligned pointers.
+"""
+import numpy as np
+import pytest
+
+import synth
+from qs_testutil import assert_keys_equal, assert_kv_sorted_equal, oracle_sort, qs_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [2, 3, 31, 32, 33, 100, 511, 512, 513, 1000, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 12_345,
+         65_543, 300_001]
+
+
+def _sort_dev(qs, x, v=None, koff=0, voff=0):
+    import torch
+
+    n = x.size
+    kbuf = to_dev(np.concatenate([np.zeros(koff, x.dtype), x]))
+    d = kbuf[koff:koff + n]
+    if v is not None:
+        vbuf = to_dev(np.concatenate([np.zeros(voff, np.int32), v]))
+        dv = vbuf[voff:voff + n]
+        qs.sort(d, dv)
+        torch.cuda.synchronize()
+        return d.cpu().numpy(), dv.cpu().numpy()
+    qs.sort(d)
+    torch.cuda.synchronize()
+    return d.cpu().numpy()
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_sort_i32_sizes(n):
+    qs = qs_gpu()
+    x = synth.uniform_i32(n, 300 + n)
+    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_sort_f64_sizes(n):
+    qs = qs_gpu()
+    x = synth.uniform_f64(n, 400 + n)
+    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_sort_kv_sizes(n):
+    qs = qs_gpu()
+    k, v = synth.kv_config("uniform", n, 500 + n)
+    gk, gv = _sort_dev(qs, k, v)
+    ok, ov = oracle_sort(k, v)
+    assert_kv_sorted_equal(k, v, gk, gv, ok, ov)
+
+
+def test_sort_i32_config_small():
+    """Single sort of one int32 array, n = 2^20, keys uniform over the full range."""
+    qs = qs_gpu()
+    x = synth.uniform_i32(1 << 20, synth.SEEDS["c1_uniform_i32"])
+    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "sorted", "reverse", "few"])
+def test_sort_f64_distributions(dist):
+    qs = qs_gpu()
+    x = synth.f64_config(dist, 1 << 20)
+    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "mod1000", "sorted", "reverse"])
+def test_sort_kv_distributions(dist):
+    qs = qs_gpu()
+    k, v = synth.kv_config(dist, 1 << 20)
+    gk, gv = _sort_dev(qs, k, v)
+    ok, ov = oracle_sort(k, v)
+    assert_kv_sorted_equal(k, v, gk, gv, ok, ov)
+    np.testing.assert_array_equal(k[gv], gk)  # value = original index: each pair intact
+
+
+@pytest.mark.parametrize("n", [100, 5000, 100_000, 1 << 20])
+def test_sort_duplicates(n):
+    qs = qs_gpu()
+    cases = [np.full(n, 7, np.int32), synth.mod_i32(n, 3, 2), synth.mod_i32(n, 4, 3) - 1,
+             np.where(synth.mod_i32(n, 5, 4) == 0, 2**31 - 1, synth.uniform_i32(n, 6)).astype(np.int32),
+             np.where(synth.mod_i32(n, 7, 3) == 0, -2**31, 2**31 - 1).astype(np.int32)]
+    for x in cases:
+        assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+
+
+@pytest.mark.parametrize("n", [500, 4096, 70_000])
+def test_sort_kv_largest_keys(n):
+    """Keys equal to the padding key must keep their own values (Section III-A-3 padding)."""
+    qs = qs_gpu()
+    k = np.where(synth.mod_i32(n, 9, 3) == 0, 2**31 - 1, synth.mod_i32(n, 10, 50)).astype(np.int32)
+    v = np.arange(n, dtype=np.int32)
+    gk, gv = _sort_dev(qs, k, v)
+    ok, ov = oracle_sort(k, v)
+    assert_kv_sorted_equal(k, v, gk, gv, ok, ov)
+    np.testing.assert_array_equal(k[gv], gk)
+
+
+def test_sort_f64_infinities():
+    qs = qs_gpu()
+    n = 50_000
+    x = synth.uniform_f64(n, 12)
+    sel = synth.mod_i32(n, 13, 10)
+    x = np.where(sel == 0, np.inf, np.where(sel == 1, -np.inf, x))
+    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+
+
+@pytest.mark.parametrize("koff,voff", [(1, 1), (1, 2), (3, 0), (2, 2)])
+def test_sort_unaligned(koff, voff):
+    qs = qs_gpu()
+    n = 100_003
+    x = synth.uniform_i32(n, 14)
+    assert_keys_equal(_sort_dev(qs, x, koff=koff), oracle_sort(x))
+    y = synth.uniform_f64(n, 15)
+    assert_keys_equal(_sort_dev(qs, y, koff=koff % 2), oracle_sort(y))
+    k, v = synth.kv_config("mod1000", n, 16)
+    gk, gv = _sort_dev(qs, k, v, koff=koff, voff=voff)
+    ok, ov = oracle_sort(k, v)
+    assert_kv_sorted_equal(k, v, gk, gv, ok, ov)
+
+
+def test_sort_workspace_reuse():
+    """Grow, shrink and alternate kinds: the workspace is reused across calls."""
+    qs = qs_gpu()
+    for n in (1 << 18, 1000, 1 << 19, 77_777, 1 << 16):
+        x = synth.uniform_i32(n, n)
+        assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+        y = synth.uniform_f64(n, n + 1)
+        assert_keys_equal(_sort_dev(qs, y), oracle_sort(y))
+
+
+def test_sort_host_buffers():
+    qs = qs_gpu()
+    x = synth.uniform_f64(200_001, 17)
+    h = x.copy()
+    qs.sort_host(h)
+    assert_keys_equal(h, oracle_sort(x))
+    k, v = synth.kv_config("uniform", 100_001, 18)
+    hk, hv = k.copy(), v.copy()
+    qs.sort_host(hk, hv)
+    ok, ov = oracle_sort(k, v)
+    assert_kv_sorted_equal(k, v, hk, hv, ok, ov)
+
+
+def test_wait_limit_reports_timeout_and_recovers():
+    """A device-side wait that runs out ends the kernel with QS_ERR_TIMEOUT
+    (no hang, no fault); the next call works."""
+    qs = qs_gpu()
+    x = synth.uniform_i32(1 << 20, 19)
+    qs.set_option("wait_limit_ns", 0)
+    try:
+        with pytest.raises(qs.QSError) as e:
+            _sort_dev(qs, x)
+        assert e.value.code == -5
+    finally:
+        qs.set_option("wait_limit_ns", 2_000_000_000)
+    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+
+
+def test_capacity_overflow_reported_and_recovers():
+    qs = qs_gpu()
+    x = synth.uniform_i32(1 << 20, 20)
+    qs.set_option("task_cap", 1)
+    try:
+        with pytest.raises(qs.QSError) as e:
+            _sort_dev(qs, x)
+        assert e.value.code == -6
+    finally:
+        qs.set_option("task_cap", 0)
+    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
