@@ -1,0 +1,438 @@
+"""Benchmark of the GB300 hybrid Quicksort (one JSON line on stdout).
+
+Headline workload: qs_sort_f64 on n = 2^28 FP64 keys uniform in [-1e6, 1e6]
+(seeded, synthetic).  One step = one in-place sort of one such array through
+the C-ABI: the persistent partition kernel (pivot selection, partition passes
+with decoupled look-back, recursion) plus the Bitonic leaf kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: every step sorts its own pristine copy of the input (2 GiB, larger
+than L2), so the K timed steps run back to back with no restore inside the
+timed region; device time comes from CUDA events on the launching stream,
+bracketed by a barrier and torch.cuda.synchronize().  With N > 1 (torchrun)
+each rank sorts its own array (replicas, weak scaling); the time is the max
+over ranks and the value counts the keys of all ranks.
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload; it is the baseline arm, not a GPU implementation.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+LOG2N = 28
+N_KEYS = 1 << LOG2N
+WORKLOAD = "f64 sort, n=2^%d, uniform [-1e6,1e6] (seed 0x5EED0002), in place"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+def _kernel_source_sha1() -> str:
+    h = hashlib.sha1()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1704_08579_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _profiled_traffic(name: str):
+    """DRAM bytes per launch recorded from an ncu capture (profiles/<name>), or
+    None when the kernel sources changed since that capture."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None, None
+    vals = {}
+    with open(p) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha1") != _kernel_source_sha1():
+        return None, vals.get("source_sha1")
+    try:
+        return float(vals["dram_bytes_per_key_per_level"]), vals.get("source_sha1")
+    except (KeyError, ValueError):
+        return None, None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id: str | None):
+        self.proc = None
+        try:
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100"]
+            if device_id:
+                cmd += ["-i", device_id]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _device_id(torch, local_rank):
+    try:
+        uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
+        return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:  # noqa: BLE001
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[local_rank] if vis else str(local_rank)
+
+
+def cpu_oracle_baseline(sample_log2: int = 24, repeats: int = 3, seed: int | None = None):
+    """Times the oracle (single-threaded Appendix A quicksort) on the first
+    2^sample_log2 keys of the workload's seeded stream."""
+    import oracle
+
+    n = 1 << sample_log2
+    x = synth.uniform_f64(n, synth.SEEDS["c2_uniform_f64"] if seed is None else seed)
+    oracle.build()
+    times = []
+    for _ in range(repeats):
+        y = x.copy()
+        t0 = time.perf_counter()
+        oracle.sort_inplace(y)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return {"value": n / t / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": "first 2^%d keys of the same seeded f64 stream, oracle quicksort, median of %d runs "
+                      "(%.2f s each)" % (sample_log2, repeats, t)}
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    n = 1 << 22  # bounded sample per step (~0.5 s of CPU work)
+    x = synth.uniform_f64(n, synth.SEEDS["c2_uniform_f64"])
+    for _ in range(args.warmup):
+        y = x.copy()
+        oracle.sort_inplace(y)
+    times = []
+    for _ in range(args.steps):
+        y = x.copy()
+        t0 = time.perf_counter()
+        oracle.sort_inplace(y)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = n / (ms / 1e3) / 1e9
+    line = {
+        "impl": "reference", "metric": "Gkeys/s sorted", "value": value, "unit": "Gkeys/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_KEYS, "sample_n": n,
+                   "note": "CPU oracle on a bounded sample of the workload (first 2^22 keys) per step"},
+        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                         "sample": "first 2^22 keys of the workload's seeded stream per step"},
+        "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _time_sorts(torch, qs, bufs, stream, vals=None):
+    """Sorts each buffer once on `stream`; returns (total ms, per-call stats)."""
+    st = []
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        start.record(stream)
+        for i, b in enumerate(bufs):
+            qs.sort(b, None if vals is None else vals[i], stream=stream)
+            st.append(qs.stats())
+        stop.record(stream)
+    stop.synchronize()
+    return start.elapsed_time(stop), st
+
+
+def _secondary(torch, qs, stream, name, make, steps=3, kind="f64"):
+    """A short measurement of another workload (not the headline)."""
+    keys = make()
+    vals = None
+    if isinstance(keys, tuple):
+        keys, vals = keys
+    n = keys.size
+    dk = torch.from_numpy(keys).to("cuda")
+    dv = torch.from_numpy(vals).to("cuda") if vals is not None else None
+    bk = [dk.clone() for _ in range(steps + 1)]
+    bv = [dv.clone() for _ in range(steps + 1)] if dv is not None else None
+    del dk, dv
+    _time_sorts(torch, qs, bk[:1], stream, None if bv is None else bv[:1])  # warm-up
+    ms, st = _time_sorts(torch, qs, bk[1:], stream, None if bv is None else bv[1:])
+    b = keys.itemsize + (4 if vals is not None else 0)
+    ms_step = ms / steps
+    drv = statistics.mean(s["ms_driver"] for s in st)
+    part_bytes = statistics.mean(s["part_keys"] for s in st) * 2 * b
+    out = {"workload": name, "n": n, "gkeys_s": n / (ms_step / 1e3) / 1e9, "ms_per_step": ms_step,
+           "partition_kernel_gbs": part_bytes / (drv / 1e3) / 1e9 if drv > 0 else None,
+           "passes_per_key": statistics.mean(s["part_keys"] for s in st) / n}
+    del bk, bv
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = _dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1704_08579_gb300 as qs
+    from paper_1704_08579_gb300 import build as qs_build
+
+    if rank == 0 or world == 1:
+        qs_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    qs_build.build()
+    qs.load()
+    hbm_peak, peak_kind = _peaks()
+
+    seed = synth.SEEDS["c2_uniform_f64"] + rank
+    host = synth.uniform_f64(N_KEYS, seed)
+    pristine = torch.from_numpy(host).to("cuda")
+    total = args.warmup + args.steps
+    bufs = [pristine.clone() for _ in range(total)]
+    stream = torch.cuda.Stream()
+    qs.reserve(N_KEYS, "f64")
+    qs.set_option("profile", 1)
+
+    # The clock sampler starts before the warm-up so that it is producing
+    # samples by the time the timed steps run.
+    sampler = ClockSampler(_device_id(torch, local)) if rank == 0 else None
+    _time_sorts(torch, qs, bufs[:args.warmup], stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms, st = _time_sorts(torch, qs, bufs[args.warmup:], stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    # sanity: every timed output is sorted (a property check, not parity)
+    for b in bufs[args.warmup:args.warmup + 2]:
+        assert bool((b[1:] >= b[:-1]).all()), "benchmark output not sorted"
+    del bufs
+    torch.cuda.empty_cache()
+
+    ms_step = ms / args.steps
+    value = world * N_KEYS / (ms_step / 1e3) / 1e9
+    drv_ms = statistics.mean(s["ms_driver"] for s in st)
+    leaf_ms = statistics.mean(s["ms_leaf"] for s in st)
+    part_keys = statistics.mean(s["part_keys"] for s in st)
+    alg_bytes = part_keys * 2 * 8  # every key of a partition task read once + written once
+    achieved = alg_bytes / (drv_ms / 1e3) / 1e9
+    traffic_per_key_level, _ = _profiled_traffic("driver_kernel_f64_2p28.md")
+    traffic = traffic_per_key_level * part_keys if traffic_per_key_level else None
+    sched_bytes = (part_keys + statistics.mean(s["leaf_keys"] + s["copy_keys"] for s in st)) * 16
+    line = {
+        "metric": "Gkeys/s sorted", "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_KEYS, "distribution": "uniform", "parallelism":
+                   "replicas" if world > 1 else "single-gpu",
+                   "l2": "inputs larger than L2: every step sorts its own 2 GiB pristine copy"},
+        "roofline": {"bound": "hbm", "kernel": "driver_kernel (persistent partition passes)",
+                     "achieved": achieved, "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": drv_ms,
+                     "passes_per_key": part_keys / N_KEYS},
+        "schedule": {"bytes_per_step": sched_bytes, "gbs_whole_step": sched_bytes / (ms_step / 1e3) / 1e9,
+                     "frac_whole_step": sched_bytes / (ms_step / 1e3) / 1e9 / hbm_peak,
+                     "lower_bound_1r1w_ms": 2 * 8 * N_KEYS / (hbm_peak * 1e9) * 1e3,
+                     "leaf_kernel_ms": leaf_ms, "driver_kernel_ms": drv_ms,
+                     "driver_cycles_last_step": st[-1]["driver_cycles"]},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        line["e2e"] = _e2e(torch, qs, host, stream, args)
+        if not args.no_extra:
+            line["extra"] = _extras(torch, qs, stream, hbm_peak)
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_oracle_baseline()
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _e2e(torch, qs, host, stream, args):
+    """Same metric through qs_sort_host_f64: pinned host buffer in, sorted host buffer out."""
+    steps = max(1, min(args.steps, 4))
+    pinned = [torch.from_numpy(host).pin_memory() for _ in range(steps + 1)]
+    arrs = [p.numpy() for p in pinned]
+    qs.sort_host(arrs[0], stream=stream)  # warm-up (allocates the staging area)
+    t0 = time.perf_counter()
+    for a in arrs[1:]:
+        qs.sort_host(a, stream=stream)
+    dt = (time.perf_counter() - t0) / steps
+    ok = bool(np.all(arrs[1][1:] >= arrs[1][:-1]))
+    del pinned, arrs
+    return {"value": N_KEYS / dt / 1e9, "unit": "Gkeys/s", "h2d_bytes_per_step": N_KEYS * 8,
+            "d2h_bytes_per_step": N_KEYS * 8, "ms_per_step": dt * 1e3, "steps": steps, "sorted": ok}
+
+
+def _extras(torch, qs, stream, hbm_peak):
+    out = []
+    n = N_KEYS
+    args_log2n = n.bit_length() - 1
+    out.append(_secondary(torch, qs, stream, "f64 sorted 2^%d" % args_log2n, lambda: synth.f64_config("sorted", n)))
+    out.append(_secondary(torch, qs, stream, "f64 reverse 2^%d" % args_log2n, lambda: synth.f64_config("reverse", n)))
+    out.append(_secondary(torch, qs, stream, "f64 16-unique 2^%d" % args_log2n, lambda: synth.f64_config("few", n)))
+    out.append(_secondary(torch, qs, stream, "i32 uniform 2^%d" % args_log2n, lambda: synth.uniform_i32(n, 0x5EED0001)))
+    out.append(_secondary(torch, qs, stream, "kv uniform 2^%d" % args_log2n, lambda: synth.kv_config("uniform", n)))
+    # qs_partition_f64 alone with the true median as pivot.
+    x = synth.f64_config("uniform", n)
+    pivot = float(np.partition(x, n // 2)[n // 2])
+    d = torch.from_numpy(x).to("cuda")
+    bufs = [d.clone() for _ in range(4)]
+    del d
+    ms_k, ms_t, split = [], [], None
+    with torch.cuda.stream(stream):
+        for i, b in enumerate(bufs):
+            split = qs.partition(b, pivot, stream=stream)
+            s = qs.stats()
+            if i:
+                ms_k.append(s["ms_driver"])
+                ms_t.append(s["ms_total"])
+    km, tm = statistics.mean(ms_k), statistics.mean(ms_t)
+    out.append({"workload": "qs_partition_f64 2^%d, pivot = true median" % args_log2n, "n": n, "split": split,
+                "kernel_ms": km, "kernel_gbs": 16 * n / (km / 1e3) / 1e9,
+                "kernel_frac": 16 * n / (km / 1e3) / 1e9 / hbm_peak,
+                "call_ms_with_copy_back": tm, "call_gkeys_s": n / (tm / 1e3) / 1e9})
+    del bufs
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_partition_only(args):
+    """qs_partition_f64 alone on the uniform input with the true median as pivot
+    (one JSON line with the per-phase cycle breakdown); used for profiling."""
+    import torch
+
+    import paper_1704_08579_gb300 as qs
+    from paper_1704_08579_gb300 import build as qs_build
+
+    qs_build.build()
+    x = synth.f64_config("uniform", N_KEYS)
+    pivot = float(np.partition(x, N_KEYS // 2)[N_KEYS // 2])
+    d = torch.from_numpy(x).to("cuda")
+    bufs = [d.clone() for _ in range(args.warmup + args.steps)]
+    del d
+    qs.set_option("profile", 1)
+    stream = torch.cuda.Stream()
+    res = []
+    with torch.cuda.stream(stream):
+        for i, b in enumerate(bufs):
+            split = qs.partition(b, pivot, stream=stream)
+            if i >= args.warmup:
+                res.append(qs.stats())
+    km = statistics.mean(r["ms_driver"] for r in res)
+    print(json.dumps({"op": "partition", "n": N_KEYS, "split": split, "kernel_ms": km,
+                      "kernel_gbs": 16 * N_KEYS / (km / 1e3) / 1e9,
+                      "driver_cycles": res[-1]["driver_cycles"], "grid": res[-1]["grid_driver"]}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--op", choices=["sort", "partition"], default="sort",
+                    help="partition: time qs_partition_f64 alone (profiling aid; not the benchmark line)")
+    ap.add_argument("--log2n", type=int, default=LOG2N,
+                    help="log2 of the keys per sort (28 = the benchmark workload; smaller only for profiling)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    global N_KEYS, WORKLOAD
+    N_KEYS = 1 << args.log2n
+    WORKLOAD = WORKLOAD % args.log2n
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.op == "partition":
+        return run_partition_only(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -131,6 +131,12 @@ typedef struct {
     double ms_leaf;         /* device time of the leaf kernel (profiling on) */
     double ms_copy;         /* device time of the partition copy-back (profiling on) */
     double ms_total;        /* device time of the whole call (profiling on) */
+    /* Profiling on: SM clock cycles the persistent kernel's CTAs spent, summed
+     * over CTAs, in [0] waiting for work, [1] waiting for a tile's keys,
+     * [2] comparing and counting, [3] the look-back, [4] staging and storing,
+     * [5] releasing the tile / waiting for the task's other tiles,
+     * [6] completing tasks (pivots, children); [7] = tiles processed. */
+    int64_t driver_cycles[8];
 } qs_stats;
 
 int qs_get_stats(qs_stats *out);

@@ -46,7 +46,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "n", "kind", "part_tasks", "part_keys", "leaf_parts", "leaf_keys", "copy_keys", "max_depth",
         "lookback_words", "grid_driver", "grid_leaf")] + [
-        (name, ctypes.c_double) for name in ("ms_driver", "ms_leaf", "ms_copy", "ms_total")]
+        (name, ctypes.c_double) for name in ("ms_driver", "ms_leaf", "ms_copy", "ms_total")] + [
+        ("driver_cycles", ctypes.c_int64 * 8)]
 
 
 def header_functions() -> list[str]:
@@ -203,7 +204,9 @@ def set_option(name: str, value: int) -> None:
 def stats() -> dict:
     st = Stats()
     _check(load().qs_get_stats(ctypes.byref(st)))
-    return {name: getattr(st, name) for name, _ in Stats._fields_}
+    out = {name: getattr(st, name) for name, _ in Stats._fields_}
+    out["driver_cycles"] = list(st.driver_cycles)
+    return out
 
 
 def version() -> int:

@@ -54,15 +54,15 @@ struct Workspace {
     void *stage_k = nullptr, *stage_v = nullptr;
     size_t stage_k_bytes = 0, stage_v_bytes = 0;
     Task *tasks = nullptr;
-    int32_t *queue = nullptr;
     int64_t task_cap = 0;
     unsigned long long *pool = nullptr;
+    int32_t *owner = nullptr;
     int64_t pool_cap = 0;
     Leaf *leaves = nullptr;
     int64_t leaf_cap = 0;
     Ctrl *ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;
-    bool dirty = true;  // look-back words / queue slots must be cleared before use
+    bool dirty = true;  // look-back words / ticket owners must be cleared before use
     cudaEvent_t ev[6] = {};
 };
 
@@ -162,21 +162,23 @@ int ws_ensure(Workspace &w, int64_t n, int kind)
     if (nd.val_bytes && (rc = grow(&w.scratch_v, &w.scratch_v_bytes, nd.val_bytes, "scratch values"))) return rc;
     const bool override_cap = g_task_cap.load() > 0;
     if (w.task_cap < nd.task_cap || (override_cap && w.task_cap != nd.task_cap)) {
-        // Task table and queue are sized together (one queue slot per task).
         if (w.tasks) cudaFree(w.tasks);
-        if (w.queue) cudaFree(w.queue);
         w.tasks = nullptr;
-        w.queue = nullptr;
         w.task_cap = 0;
-        size_t have_t = 0, have_q = 0;
+        size_t have_t = 0;
         if ((rc = grow(reinterpret_cast<void **>(&w.tasks), &have_t, nd.task_cap * sizeof(Task), "tasks"))) return rc;
-        if ((rc = grow(reinterpret_cast<void **>(&w.queue), &have_q, nd.task_cap * sizeof(int32_t), "queue"))) return rc;
         w.task_cap = nd.task_cap;
-        w.dirty = true;
     }
     if (w.pool_cap < nd.pool_cap) {
-        size_t have = w.pool ? static_cast<size_t>(w.pool_cap) * 8 : 0;
-        if ((rc = grow(reinterpret_cast<void **>(&w.pool), &have, nd.pool_cap * 8, "look-back words"))) return rc;
+        // Look-back words and ticket owners are sized together.
+        if (w.pool) cudaFree(w.pool);
+        if (w.owner) cudaFree(w.owner);
+        w.pool = nullptr;
+        w.owner = nullptr;
+        w.pool_cap = 0;
+        size_t have_p = 0, have_o = 0;
+        if ((rc = grow(reinterpret_cast<void **>(&w.pool), &have_p, nd.pool_cap * 8, "look-back words"))) return rc;
+        if ((rc = grow(reinterpret_cast<void **>(&w.owner), &have_o, nd.pool_cap * 4, "ticket owners"))) return rc;
         w.pool_cap = nd.pool_cap;
         w.dirty = true;
     }
@@ -192,7 +194,7 @@ void ws_free(Workspace &w)
 {
     if (!w.init) return;
     cudaDeviceSynchronize();
-    void *bufs[] = {w.scratch_k, w.scratch_v, w.stage_k, w.stage_v, w.tasks, w.queue, w.pool, w.leaves, w.ctrl};
+    void *bufs[] = {w.scratch_k, w.scratch_v, w.stage_k, w.stage_v, w.tasks, w.owner, w.pool, w.leaves, w.ctrl};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (w.h_ctrl) cudaFreeHost(w.h_ctrl);
@@ -201,7 +203,7 @@ void ws_free(Workspace &w)
     w.scratch_k = w.scratch_v = w.stage_k = w.stage_v = nullptr;
     w.scratch_k_bytes = w.scratch_v_bytes = w.stage_k_bytes = w.stage_v_bytes = 0;
     w.tasks = nullptr;
-    w.queue = nullptr;
+    w.owner = nullptr;
     w.pool = nullptr;
     w.leaves = nullptr;
     w.ctrl = nullptr;
@@ -259,7 +261,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     if (w.dirty) {
         if ((e = cudaMemsetAsync(w.pool, 0, static_cast<size_t>(w.pool_cap) * 8, s)) != cudaSuccess)
             return cuda_fail(e, "cudaMemsetAsync");
-        if ((e = cudaMemsetAsync(w.queue, 0, static_cast<size_t>(w.task_cap) * 4, s)) != cudaSuccess)
+        if ((e = cudaMemsetAsync(w.owner, 0, static_cast<size_t>(w.pool_cap) * 4, s)) != cudaSuccess)
             return cuda_fail(e, "cudaMemsetAsync");
         w.dirty = false;
     }
@@ -276,7 +278,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     }
     a.n = n;
     a.tasks = w.tasks;
-    a.queue = w.queue;
+    a.owner = w.owner;
     a.pool = w.pool;
     a.leaves = w.leaves;
     a.ctrl = w.ctrl;
@@ -288,6 +290,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     a.wait_limit_ns = static_cast<uint64_t>(g_wait_limit_ns.load());
     a.pivot_bits = pivot_bits;
     a.partition_only = partition_only;
+    a.profile = g_profile.load();
 
     LaunchCfg cfg;
     std::memset(&cfg, 0, sizeof(cfg));
@@ -317,6 +320,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     t_stats.lookback_words = static_cast<int64_t>(c.pool_cursor);
     t_stats.grid_driver = cfg.grid_driver;
     t_stats.grid_leaf = cfg.grid_leaf;
+    for (int i = 0; i < 8; ++i) t_stats.driver_cycles[i] = static_cast<int64_t>(c.cycles[i]);
     if (c.status != 0) {
         w.dirty = true;
         return fail(c.status, "%s (code %d, detail %d)", status_text(c.status), c.status, c.info);
@@ -384,11 +388,14 @@ int run_host(int kind, K *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream
 }
 
 uint64_t bits_i32(int32_t k) { return static_cast<uint64_t>(static_cast<int64_t>(k)); }
+// The kernels compare doubles in sort space: the IEEE bits with the sign bit
+// flipped for non-negative values and every bit flipped for negative ones.
 uint64_t bits_f64(double k)
 {
+    if (k == 0.0) k = 0.0;  // a -0.0 pivot splits exactly like +0.0
     uint64_t b;
     std::memcpy(&b, &k, 8);
-    return b;
+    return b ^ (static_cast<uint64_t>(static_cast<int64_t>(b) >> 63) | 0x8000000000000000ull);
 }
 
 }  // namespace

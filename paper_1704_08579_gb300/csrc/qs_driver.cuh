@@ -1,0 +1,834 @@
+// Persistent partition driver (Section III-C, Algorithm 3, made device-side)
+// and its partition tile (Section III-B).
+//
+// Work model: a partition task is cut into tiles of T keys.  When a task is
+// created it reserves a contiguous range of global tickets (its look-back
+// words) and publishes, for every ticket, the id of the task.  CTAs claim
+// tickets in increasing order with one atomic each; a ticket whose task is
+// not published yet is simply waited for.  Every wait therefore points to a
+// lower ticket (a tile waits for earlier tiles of its task; a claimed ticket
+// waits only for the CTA's current, lower ticket), so waits cannot form a
+// cycle.  A CTA claims its next ticket while it still processes the current
+// tile and, if that tile is known, prefetches its keys (and values) into
+// shared memory with a 1-D TMA bulk copy, so loads overlap the scan, the
+// look-back and the stores.
+//
+// Partition order inside a task (fixed so the result is deterministic): keys
+// going to the lower side keep input order; keys going to the upper side are
+// written from the end of the range backwards, i.e. in reverse input order --
+// what one pass with a left write cursor and a right write cursor produces
+// (the paper's left_w / right_w).
+//
+// The CTA that processes the last tile of a task waits until every other tile
+// of the task has released its stores, then completes the task: it picks the
+// pivots of the children (median of 64 sampled keys) and queues them, or lists
+// them for the Bitonic kernel when they hold at most leaf_max keys.
+#pragma once
+
+#include "qs_bitonic.cuh"
+#include "qs_common.cuh"
+
+namespace qs {
+
+// ---------------------------------------------------------------------------
+// Pivot selection.  The paper's experiments use a median of three values
+// (Section IV-A); here the median of 64 keys sampled at jittered strides over
+// the range, sorted by one warp with the Bitonic network.  Called by a full
+// warp; returns the pivot in sort space, as bits.
+// ---------------------------------------------------------------------------
+template <class K>
+__device__ uint64_t sample_median(const K *src, int64_t off, int64_t len, uint64_t salt)
+{
+    using Ops = KeyOps<K>;
+    using S = typename Ops::S;
+    const int lane = threadIdx.x & 31;
+    S s[2];
+    int32_t dummy[2] = {0, 0};
+    const int64_t stride = len / 64;  // len > 64 for every partition task
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int i = lane * 2 + r;
+        const uint64_t h = mix64(salt * 64 + i);
+        const int64_t jitter = static_cast<int64_t>(h % static_cast<uint64_t>(stride > 0 ? stride : 1));
+        s[r] = Ops::to_s(__ldcg(src + off + (static_cast<int64_t>(i) * len) / 64 + jitter));
+    }
+    warp_bitonic_sort<2, S, int32_t, false>(s, dummy);
+    return Ops::s_to_bits(__shfl_sync(0xffffffffu, s[0], 16));  // element 32 of 64
+}
+
+// ---------------------------------------------------------------------------
+// Task creation and leaf listing (called by one thread).
+// ---------------------------------------------------------------------------
+struct NewTask {
+    long long id;
+    long long g0;  // first ticket / look-back word
+    long long ntiles;
+};
+
+// Thread 0: allocates a task and its tickets and writes its fields.  The
+// tickets become claimable once publish_task() has run.
+template <class Tr>
+__device__ bool alloc_task(const Args<typename Tr::K, typename Tr::V> &a, int64_t off, int64_t len, int src,
+                           uint64_t pivot_bits, int mode, int depth, NewTask &nt)
+{
+    Ctrl *c = a.ctrl;
+    if (depth > kMaxDepth) {
+        set_error(c, kErrDepth, depth);
+        return false;
+    }
+    const unsigned long long id = atomicAdd(&c->n_tasks, 1ull);
+    if (id >= static_cast<unsigned long long>(a.task_cap)) {
+        set_error(c, kErrCapacity, 1);
+        return false;
+    }
+    const int64_t w0 = off - ((a.key_phase[src] + off) % Tr::VW);
+    const int64_t ntiles = (off + len - w0 + Tr::T - 1) / Tr::T;
+    const unsigned long long g0 = atomicAdd(&c->pool_cursor, static_cast<unsigned long long>(ntiles));
+    if (g0 + ntiles > static_cast<unsigned long long>(a.pool_cap)) {
+        set_error(c, kErrCapacity, 2);
+        return false;
+    }
+    Task *t = a.tasks + id;
+    t->off = off;
+    t->len = len;
+    t->w0 = w0;
+    t->pool = static_cast<int64_t>(g0);
+    t->pivot = pivot_bits;
+    t->ntiles = static_cast<int32_t>(ntiles);
+    t->src = src;
+    t->mode = mode;
+    t->depth = depth;
+    t->next_tile = 0;
+    t->tiles_done = 0;
+    t->eq = 0;
+    t->lt_total = 0;
+    __threadfence();
+    atomicAdd(&c->part_tasks, 1ull);
+    atomicAdd(&c->part_keys, static_cast<unsigned long long>(len));
+    atomicMax(&c->max_depth, static_cast<unsigned long long>(depth));
+    nt.id = static_cast<long long>(id);
+    nt.g0 = static_cast<long long>(g0);
+    nt.ntiles = ntiles;
+    return true;
+}
+
+// Whole CTA, after alloc_task() and a barrier: makes the task's tickets
+// claimable.
+__device__ __forceinline__ void publish_task(const int32_t *owner_c, const NewTask &nt)
+{
+    int32_t *owner = const_cast<int32_t *>(owner_c);
+    __threadfence();  // order the task's fields (written by thread 0) before its tickets
+    for (long long i = threadIdx.x; i < nt.ntiles; i += kThreads)
+        asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(owner + nt.g0 + i), "r"(static_cast<int>(nt.id) + 1)
+                     : "memory");
+}
+
+// Reserves `count` leaf entries on the large (front) or small (back) side.
+// Returns the first index, or -1 on overflow (error recorded).
+template <class Tr>
+__device__ int64_t reserve_leaves(const Args<typename Tr::K, typename Tr::V> &a, int64_t count, bool small)
+{
+    Ctrl *c = a.ctrl;
+    const unsigned long long used = small ? atomicAdd(&c->n_small, static_cast<unsigned long long>(count))
+                                          : atomicAdd(&c->n_large, static_cast<unsigned long long>(count));
+    // Both sides share one array; check the combined fill after reserving.
+    const unsigned long long other = small ? ld_relaxed_u64(&c->n_large) : ld_relaxed_u64(&c->n_small);
+    if (used + count + other > static_cast<unsigned long long>(a.leaf_cap)) {
+        set_error(c, kErrCapacity, 3);
+        return -1;
+    }
+    return small ? a.leaf_cap - 1 - static_cast<int64_t>(used) : static_cast<int64_t>(used);
+}
+
+template <class Tr>
+__device__ void push_leaf(const Args<typename Tr::K, typename Tr::V> &a, int64_t off, int64_t len, int flags)
+{
+    const bool small = len <= a.small_max;
+    const int64_t i = reserve_leaves<Tr>(a, 1, small);
+    if (i < 0) return;
+    Leaf l;
+    l.off = off;
+    l.len = static_cast<int32_t>(len);
+    l.flags = flags;
+    a.leaves[i] = l;
+    if (!(flags & kLeafFinal)) {
+        atomicAdd(&a.ctrl->leaf_parts, 1ull);
+        atomicAdd(&a.ctrl->leaf_keys, static_cast<unsigned long long>(len));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Shared memory of the persistent kernel.
+// ---------------------------------------------------------------------------
+struct WorkItem {
+    int kind;  // 0 none/exit, 1 tile
+    int task;
+    long long ticket;
+    int tile;
+    int ntiles;
+    int src, mode;
+    int full;   // tile lies entirely inside the task: TMA bulk load
+    int a_pub;  // its look-back aggregate was already published (early count)
+    int64_t off, len, w0, pool;
+    uint64_t pivot;
+};
+
+template <class Tr>
+struct DriverSmem {
+    alignas(128) typename Tr::K kbuf[2][Tr::T];
+    alignas(128) typename Tr::V vbuf[2][Tr::KV ? Tr::T : 4];
+    alignas(8) unsigned long long bar[2];
+    int wcount[Tr::VPT * kWarps];
+    long long excl;
+    long long first;
+    int low_total;
+    int eq_total;
+    int next_low;  // early count of the prefetched tile (warps 1..7)
+    int last;
+    int abort;
+    WorkItem w[2];  // [0] current, [1] next
+    long long next_ticket;  // claimed ticket whose task was not published yet
+    NewTask nt[2];
+    int nt_ok[2];
+    int64_t c_off[2], c_len[2];
+    int c_kind[2];  // 0 none, 1 finished (equal keys), 2 leaf, 3 partition (sampled pivot), 4 partition ('<=', same pivot)
+};
+
+template <class Tr>
+__device__ __forceinline__ void fill_tile(const Args<typename Tr::K, typename Tr::V> &a, WorkItem &w)
+{
+    const int64_t base = w.w0 + static_cast<int64_t>(w.tile) * Tr::T;
+    w.full = base >= w.off && base + Tr::T <= w.off + w.len && (!Tr::KV || a.val_vec[w.src]);
+}
+
+// Issues the TMA bulk load of a full tile into buffer `b` (thread 0).
+template <class Tr>
+__device__ __forceinline__ void issue_tile_load(const Args<typename Tr::K, typename Tr::V> &a, const WorkItem &w,
+                                                DriverSmem<Tr> &sm, int b)
+{
+    if (!w.full) return;
+    const int64_t base = w.w0 + static_cast<int64_t>(w.tile) * Tr::T;
+    constexpr uint32_t kb = Tr::T * sizeof(typename Tr::K);
+    constexpr uint32_t vb = Tr::KV ? Tr::T * sizeof(typename Tr::V) : 0;
+    fence_proxy_async_smem();  // the buffer was last touched by ordinary loads/stores
+    mbar_arrive_expect_tx(&sm.bar[b], kb + vb);
+    bulk_g2s(sm.kbuf[b], a.keys[w.src] + base, kb, &sm.bar[b]);
+    if constexpr (Tr::KV) bulk_g2s(sm.vbuf[b], a.vals[w.src] + base, vb, &sm.bar[b]);
+}
+
+// Thread 0: the tile of ticket g if its task is published (kind 1), else
+// kind 0.  `hint` avoids re-reading the fields of the task already in hand.
+template <class Tr>
+__device__ WorkItem try_resolve(const Args<typename Tr::K, typename Tr::V> &a, long long g, const WorkItem &hint)
+{
+    WorkItem w = hint;
+    w.kind = 0;
+    w.ticket = g;
+    if (g >= a.pool_cap) return w;  // beyond every ticket that can be published
+    const int id1 = ld_acquire_s32(a.owner + g);
+    if (id1 <= 0 || id1 > a.task_cap) {
+        if (id1 != 0) set_error(a.ctrl, kErrInternalIndex, 2);
+        return w;
+    }
+    if (!(hint.kind == 1 && hint.task == id1 - 1)) {
+        const Task *t = a.tasks + (id1 - 1);
+        w.task = id1 - 1;
+        w.ntiles = __ldcg(&t->ntiles);
+        w.src = __ldcg(&t->src);
+        w.mode = __ldcg(&t->mode);
+        w.off = __ldcg(&t->off);
+        w.len = __ldcg(&t->len);
+        w.w0 = __ldcg(&t->w0);
+        w.pool = __ldcg(&t->pool);
+        w.pivot = __ldcg(reinterpret_cast<const unsigned long long *>(&t->pivot));
+    }
+    w.tile = static_cast<int>(g - w.pool);
+    if (w.tile < 0 || w.tile >= w.ntiles) {
+        set_error(a.ctrl, kErrInternalIndex, 6);
+        return w;
+    }
+    w.kind = 1;
+    w.a_pub = 0;
+    fill_tile<Tr>(a, w);
+    return w;
+}
+
+// Thread 0: waits (bounded) until ticket g's task is published; kind 0 means
+// exit (no partition task is pending any more, or an error was reported).
+template <class Tr>
+__device__ WorkItem resolve_blocking(const Args<typename Tr::K, typename Tr::V> &a, long long g, const WorkItem &hint)
+{
+    Ctrl *c = a.ctrl;
+    uint64_t t0 = 0;
+    unsigned ns = 32;
+    for (;;) {
+        WorkItem w = try_resolve<Tr>(a, g, hint);
+        if (w.kind == 1 || ld_relaxed_s32(&c->status) != 0) {
+            if (ld_relaxed_s32(&c->status) != 0) w.kind = 0;
+            return w;
+        }
+        // No task left at all: ticket g will never be published.
+        if (ld_relaxed_s64(&c->pending) == 0) return w;
+        const uint64_t now = global_ns();
+        if (t0 == 0) {
+            t0 = now;
+        } else if (now - t0 > a.wait_limit_ns) {
+            set_error(c, kErrTimeout, 1);
+            w.kind = 0;
+            return w;
+        }
+        __nanosleep(ns);
+        ns = ns < 512 ? ns * 2 : ns;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Decoupled look-back by warp 0 (Merrill & Garland).  Returns the number of
+// lower-side keys in all preceding tiles of the task, or -1 if the wait ran
+// out or another CTA reported an error.
+// ---------------------------------------------------------------------------
+static __device__ long long lookback(unsigned long long *words, int tile, unsigned long long low, Ctrl *c,
+                                     uint64_t limit_ns, bool published)
+{
+    const int lane = threadIdx.x & 31;
+    if (tile == 0) {
+        if (lane == 0 && !published) st_relaxed_u64(words, kFlagPrefix | low);
+        return 0;
+    }
+    if (lane == 0 && !published) st_relaxed_u64(words + tile, kFlagAggregate | low);
+    long long excl = 0;
+    int idx = tile - 1;  // lane l looks at tile idx - l
+    uint64_t t0 = 0;
+    int spins = 0;
+    unsigned long long s = idx - lane >= 0 ? ld_relaxed_u64(words + (idx - lane)) : kFlagPrefix;
+    for (;;) {
+        const unsigned flag = static_cast<unsigned>(s >> 62);
+        const unsigned notready = __ballot_sync(0xffffffffu, flag == 0);
+        const unsigned pmask = __ballot_sync(0xffffffffu, flag == 2);
+        const int first_nr = notready ? __ffs(notready) - 1 : 32;
+        const int first_p = pmask ? __ffs(pmask) - 1 : 32;
+        if (first_p < first_nr || first_nr == 32) {
+            // Lanes 0..last form a ready run: add their counts.
+            const int last = first_p < first_nr ? first_p : 31;
+            long long v = lane <= last ? static_cast<long long>(s & kCountMask) : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            excl += v;
+            if (first_p < first_nr) break;  // reached an inclusive prefix
+            idx -= 32;
+            const int j = idx - lane;
+            s = j >= 0 ? ld_relaxed_u64(words + j) : kFlagPrefix;
+            continue;
+        }
+        // A tile before the nearest prefix has not published yet: re-read it.
+        if (flag == 0) s = ld_relaxed_u64(words + (idx - lane));
+        if (++spins == 64) {
+            spins = 0;
+            int bad = 0;
+            if (lane == 0) {
+                const uint64_t now = global_ns();
+                if (t0 == 0) t0 = now;
+                const bool late = now - t0 > limit_ns;
+                if (late) set_error(c, kErrTimeout, 2);
+                bad = late || ld_relaxed_s32(&c->status) != 0;
+            }
+            if (__shfl_sync(0xffffffffu, bad, 0)) return -1;
+        }
+    }
+    if (lane == 0) st_relaxed_u64(words + tile, kFlagPrefix | static_cast<unsigned long long>(excl + low));
+    return excl;
+}
+
+// ---------------------------------------------------------------------------
+// One partition tile.  Vector k of thread t covers tile positions
+// k*NT*VW + t*VW + j, so the input order is (k, warp, lane, j).  The pivot
+// compare (the paper's vector compare into a mask) becomes warp ballots whose
+// popcounts give every key its rank among the tile's lower-side keys; a CTA
+// scan of the (k, warp) counts plus the look-back give its global position.
+// Keys are staged in shared memory in output order and written with
+// coalesced stores.  Returns 1 if this CTA completes the task, 0 if not, -1
+// on abort.
+// ---------------------------------------------------------------------------
+template <class Tr>
+__device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, const WorkItem &w, WorkItem &nx,
+                              DriverSmem<Tr> &sm, int b, uint32_t &phases, long long *tm)
+{
+    using K = typename Tr::K;
+    using V = typename Tr::V;
+    using Ops = KeyOps<K>;
+    using S = typename Ops::S;
+    using Vec = typename Ops::Vec;
+    constexpr int VW = Tr::VW, VPT = Tr::VPT, T = Tr::T, E = Tr::E;
+    constexpr int NC = VPT * kWarps;       // (vector, warp) chunk counts
+    constexpr int CPL = (NC + 31) / 32;    // chunk counts per lane in the scan
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    K *__restrict__ dk = a.keys[w.src ^ 1];
+    V *__restrict__ dv = a.vals[w.src ^ 1];
+    const int64_t off = w.off, end = w.off + w.len;
+    const int64_t base = w.w0 + static_cast<int64_t>(w.tile) * T;
+    const S pivot = Ops::s_from_bits(w.pivot);
+    const bool le = w.mode == kModeLessEqual;
+
+    K key[E];
+    V val[Tr::KV ? E : 1];
+    uint32_t lowm = 0, validm = 0;
+
+    long long tprev = a.profile ? clock64() : 0;
+#define QS_TICK(slot)                         \
+    if (a.profile) {                          \
+        const long long tnow_ = clock64();    \
+        tm[slot] += tnow_ - tprev;            \
+        tprev = tnow_;                        \
+    }
+    if (w.full) {
+        if (!mbar_wait_bounded(&sm.bar[b], (phases >> b) & 1u, a.ctrl, a.wait_limit_ns)) return -1;
+        phases ^= 1u << b;
+        QS_TICK(1);
+        const Vec *sv = reinterpret_cast<const Vec *>(sm.kbuf[b]);
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            K tmp[VW];
+            Ops::split(sv[k * kThreads + tid], tmp);
+#pragma unroll
+            for (int j = 0; j < VW; ++j) key[k * VW + j] = tmp[j];
+            if constexpr (Tr::KV) {
+                const int4 vv = reinterpret_cast<const int4 *>(sm.vbuf[b])[k * kThreads + tid];
+                val[k * VW + 0] = vv.x;
+                val[k * VW + 1] = vv.y;
+                val[k * VW + 2] = vv.z;
+                val[k * VW + 3] = vv.w;
+            }
+        }
+        validm = E == 32 ? 0xffffffffu : ((1u << E) - 1u);
+    } else {
+        const K *__restrict__ sk = a.keys[w.src];
+        const V *__restrict__ svv = a.vals[w.src];
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            const int64_t e = base + static_cast<int64_t>(k) * kThreads * VW + tid * VW;
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                const int64_t p = e + j;
+                const bool ok = p >= off && p < end;
+                key[k * VW + j] = ok ? __ldcg(sk + p) : K(0);
+                if constexpr (Tr::KV) val[k * VW + j] = ok ? __ldcg(svv + p) : 0;
+                validm |= ok ? (1u << (k * VW + j)) : 0u;
+            }
+        }
+    }
+    int eq = 0;
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const S s = Ops::to_s(key[i]);
+        const bool v = (validm >> i) & 1u;
+        const bool lo = v && (le ? !(pivot < s) : s < pivot);
+        lowm |= lo ? (1u << i) : 0u;
+        eq += (v && s == pivot) ? 1 : 0;
+    }
+
+    // Warp ballots -> rank of each key among the lower-side keys of its (k, warp) chunk.
+    int rank[VPT];
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+        int tot = 0, pre = 0;
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+            const unsigned bb = __ballot_sync(0xffffffffu, (lowm >> (k * VW + j)) & 1u);
+            tot += __popc(bb);
+            pre += __popc(bb & lt_mask);
+        }
+        rank[k] = pre;
+        if (lane == 0) sm.wcount[k * kWarps + warp] = tot;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) eq += __shfl_xor_sync(0xffffffffu, eq, o);
+    if (lane == 0 && eq) atomicAdd(&sm.eq_total, eq);
+    __syncthreads();
+    QS_TICK(2);
+
+    // Warp 0: exclusive scan of the chunk counts, then the look-back.
+    if (warp == 0) {
+        int v[CPL];
+        int sum = 0;
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            const int idx = lane * CPL + i;
+            v[i] = idx < NC ? sm.wcount[idx] : 0;
+            sum += v[i];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int n = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += n;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        int run = incl - sum;
+#pragma unroll
+        for (int i = 0; i < CPL; ++i) {
+            const int idx = lane * CPL + i;
+            if (idx < NC) sm.wcount[idx] = run;
+            run += v[i];
+        }
+        const long long excl = lookback(a.pool + w.pool, w.tile, static_cast<unsigned long long>(total), a.ctrl,
+                                        a.wait_limit_ns, w.a_pub != 0);
+        if (lane == 0) {
+            sm.excl = excl;
+            sm.low_total = total;
+            sm.abort = excl < 0;
+            if (excl >= 0 && w.tile == w.ntiles - 1)
+                st_relaxed_u64(&a.tasks[w.task].lt_total, static_cast<unsigned long long>(excl + total));
+        }
+    } else if (nx.kind == 1 && nx.full && !nx.a_pub) {
+        // Meanwhile warps 1..7 count the prefetched next tile and publish its
+        // aggregate at once, so tiles after it never wait for this CTA to
+        // finish the current tile.
+        if (mbar_wait_bounded(&sm.bar[b ^ 1], (phases >> (b ^ 1)) & 1u, a.ctrl, a.wait_limit_ns)) {
+            const S npiv = Ops::s_from_bits(nx.pivot);
+            const bool nle = nx.mode == kModeLessEqual;
+            const K *nk = sm.kbuf[b ^ 1];
+            int cnt = 0;
+            for (int i = tid - 32; i < T; i += kThreads - 32) {
+                const S s = Ops::to_s(nk[i]);
+                cnt += (nle ? !(npiv < s) : s < npiv) ? 1 : 0;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (lane == 0) atomicAdd(&sm.next_low, cnt);
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(kThreads - 32) : "memory");
+        if (tid == 32) {
+            const unsigned long long c = static_cast<unsigned long long>(sm.next_low);
+            st_relaxed_u64(a.pool + nx.pool + nx.tile, (nx.tile == 0 ? kFlagPrefix : kFlagAggregate) | c);
+            sm.next_low = 0;
+            nx.a_pub = 1;
+        }
+    }
+    __syncthreads();
+    QS_TICK(3);
+    if (sm.abort) return -1;
+
+    const int L = sm.low_total;
+    const long long excl = sm.excl;
+    const int64_t vstart = base > off ? base : off;
+    const int64_t vend = base + T < end ? base + T : end;
+    const int nvalid = static_cast<int>(vend - vstart);
+    K *stage_k = sm.kbuf[b];
+    V *stage_v = sm.vbuf[b];
+
+    // Stage in output order: lower-side keys at [0, L), upper-side keys after.
+#pragma unroll
+    for (int k = 0; k < VPT; ++k) {
+        int r = sm.wcount[k * kWarps + warp] + rank[k];
+        const int64_t e = base + static_cast<int64_t>(k) * kThreads * VW + tid * VW;
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+            const int i = k * VW + j;
+            const bool lo = (lowm >> i) & 1u;
+            if ((validm >> i) & 1u) {
+                const int q = static_cast<int>(e + j - vstart);  // position among valid keys
+                const int s = lo ? r : L + (q - r);
+                stage_k[s] = key[i];
+                if constexpr (Tr::KV) stage_v[s] = val[i];
+            }
+            r += lo ? 1 : 0;
+        }
+    }
+    __syncthreads();
+
+    const int64_t hpre = (vstart - off) - excl;  // upper-side keys in earlier tiles
+    bool bad = false;
+    for (int s = tid; s < nvalid; s += kThreads) {
+        const int64_t d = s < L ? off + excl + s : end - 1 - (hpre + (s - L));
+        if (d < off || d >= end) {  // never taken when the scan is consistent
+            bad = true;
+            continue;
+        }
+        dk[d] = stage_k[s];
+        if constexpr (Tr::KV) dv[d] = stage_v[s];
+    }
+    if (bad) set_error(a.ctrl, kErrInternalIndex, 1);
+    __syncthreads();
+    QS_TICK(4);
+    if (tid == 0) {
+        Task *t = a.tasks + w.task;
+        if (sm.eq_total) atomicAdd(&t->eq, static_cast<unsigned long long>(sm.eq_total));
+        sm.eq_total = 0;
+        __threadfence();  // release this tile's stores
+        int last = 0;
+        if (w.tile != w.ntiles - 1) {
+            atomicAdd(&t->tiles_done, 1ull);
+        } else {
+            // The last tile completes the task once every other tile has released.
+            last = 1;
+            const unsigned long long want = static_cast<unsigned long long>(w.ntiles - 1);
+            if (ld_acquire_u64(&t->tiles_done) != want) {
+                const uint64_t t0 = global_ns();
+                unsigned ns = 32;
+                while (ld_acquire_u64(&t->tiles_done) != want) {
+                    if (global_ns() - t0 > a.wait_limit_ns || ld_relaxed_s32(&a.ctrl->status) != 0) {
+                        set_error(a.ctrl, kErrTimeout, 5);
+                        last = -1;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    ns = ns < 512 ? ns * 2 : ns;
+                }
+            }
+            __threadfence();
+        }
+        sm.last = last;
+    }
+    __syncthreads();
+    QS_TICK(5);
+#undef QS_TICK
+    tm[7] += 1;
+    return sm.last;
+}
+
+// ---------------------------------------------------------------------------
+// Completing a task (whole CTA): decide the children, pick their pivots,
+// queue them or list them as leaves.  Algorithm 3 recurses on both sides; a
+// side of at most leaf_max keys goes to the Bitonic kernel.
+// Equal keys (the paper is silent on duplicates): with the '<' rule nothing
+// moves when the pivot is the smallest key of the range; the range is then
+// partitioned again with '<=', whose lower side holds only keys equal to the
+// pivot and is finished.  A side known to hold only keys equal to the pivot
+// (its size equals the count of pivot-equal keys) is finished too.
+// ---------------------------------------------------------------------------
+template <class Tr>
+__device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const WorkItem &w, DriverSmem<Tr> &sm)
+{
+    using K = typename Tr::K;
+    const int tid = threadIdx.x;
+    Task *t = a.tasks + w.task;
+    const int dst = w.src ^ 1;
+    if (tid == 0) {
+        const int64_t lt = static_cast<int64_t>(ld_relaxed_u64(&t->lt_total));
+        const int64_t eq = static_cast<int64_t>(ld_relaxed_u64(&t->eq));
+        const int64_t off = w.off, len = w.len;
+        sm.c_kind[0] = sm.c_kind[1] = 0;
+        if (a.partition_only) {
+            a.ctrl->lt_result = static_cast<unsigned long long>(lt);
+        } else if (w.mode == kModeLess) {
+            if (lt == 0) {
+                sm.c_off[0] = off;
+                sm.c_len[0] = len;
+                sm.c_kind[0] = (eq == len) ? 1 : 4;
+            } else {
+                sm.c_off[0] = off;
+                sm.c_len[0] = lt;
+                sm.c_kind[0] = 3;
+                sm.c_off[1] = off + lt;
+                sm.c_len[1] = len - lt;
+                sm.c_kind[1] = (len - lt == eq) ? 1 : 3;
+            }
+        } else {  // '<=' pass after a '<' pass that moved nothing: lower side == pivot
+            sm.c_off[0] = off;
+            sm.c_len[0] = lt;
+            sm.c_kind[0] = 1;
+            sm.c_off[1] = off + lt;
+            sm.c_len[1] = len - lt;
+            sm.c_kind[1] = 3;
+        }
+        for (int i = 0; i < 2; ++i) {
+            if (sm.c_kind[i] == 0) continue;
+            if (sm.c_len[i] <= 0) {
+                sm.c_kind[i] = 0;
+                continue;
+            }
+            if ((sm.c_kind[i] == 3 || sm.c_kind[i] == 4) && sm.c_len[i] <= a.leaf_max) sm.c_kind[i] = 2;
+        }
+    }
+    __syncthreads();
+    // Children that are partition tasks: pivots first (warp 0), then thread 0
+    // allocates both, then the whole CTA publishes their tickets.
+    uint64_t pbits[2] = {w.pivot, w.pivot};
+    if (tid < 32) {
+        for (int i = 0; i < 2; ++i)
+            if (sm.c_kind[i] == 3)
+                pbits[i] = sample_median<K>(a.keys[dst], sm.c_off[i], sm.c_len[i],
+                                            static_cast<uint64_t>(sm.c_off[i]) * 0x2545F4914F6CDD1Dull + sm.c_len[i]);
+    }
+    if (tid == 0) {
+        int nbig = 0;
+        for (int i = 0; i < 2; ++i) {
+            sm.nt_ok[i] = 0;
+            const int kind = sm.c_kind[i];
+            if (kind == 3 || kind == 4) {
+                sm.nt_ok[i] = alloc_task<Tr>(a, sm.c_off[i], sm.c_len[i], dst, pbits[i],
+                                             kind == 4 ? kModeLessEqual : kModeLess, __ldcg(&t->depth) + 1, sm.nt[i]);
+                nbig += sm.nt_ok[i];
+            } else if (kind == 2) {
+                push_leaf<Tr>(a, sm.c_off[i], sm.c_len[i], dst == 1 ? kLeafScratch : 0);
+            }
+        }
+        sm.low_total = nbig;
+    }
+    __syncthreads();
+    for (int i = 0; i < 2; ++i)
+        if (sm.nt_ok[i]) publish_task(a.owner, sm.nt[i]);
+    for (int i = 0; i < 2; ++i) {
+        // Finished run of equal keys: copy back only if it sits in scratch.
+        if (sm.c_kind[i] != 1 || dst != 1) continue;
+        const int64_t coff = sm.c_off[i], clen = sm.c_len[i];
+        const bool small = clen <= a.small_max;
+        const int64_t chunks = small ? 1 : (clen + kCopyChunk - 1) / kCopyChunk;
+        __syncthreads();
+        if (tid == 0) {
+            sm.first = reserve_leaves<Tr>(a, chunks, small);
+            atomicAdd(&a.ctrl->copy_keys, static_cast<unsigned long long>(clen));
+        }
+        __syncthreads();
+        const long long first = sm.first;
+        if (first >= 0) {
+            for (int64_t q = tid; q < chunks; q += kThreads) {
+                Leaf l;
+                l.off = coff + q * kCopyChunk;
+                const int64_t rem = clen - q * kCopyChunk;
+                l.len = static_cast<int32_t>(small ? clen : (rem < kCopyChunk ? rem : kCopyChunk));
+                l.flags = kLeafFinal | kLeafScratch;
+                a.leaves[small ? first : first + q] = l;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // This task is done; its partition children are pending.
+        atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctrl->pending),
+                  static_cast<unsigned long long>(static_cast<long long>(sm.low_total) - 1));
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Persistent partition kernel.
+// ---------------------------------------------------------------------------
+template <class Tr, int MinBlocks>
+__global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typename Tr::K, typename Tr::V> a)
+{
+    extern __shared__ __align__(128) unsigned char dyn_smem[];
+    DriverSmem<Tr> &sm = *reinterpret_cast<DriverSmem<Tr> *>(dyn_smem);
+    const int tid = threadIdx.x;
+    uint32_t phases = 0;   // bit b: parity of the next completion of bar[b]
+    uint32_t pending = 0;  // bit b: a bulk load into buffer b is issued and not yet consumed
+    long long tm[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per-phase cycles (thread 0, profiling on)
+    long long t_wait = a.profile ? clock64() : 0;
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+        sm.eq_total = 0;
+        sm.next_low = 0;
+        WorkItem none;
+        none.kind = 0;
+        const long long g = static_cast<long long>(atomicAdd(&a.ctrl->ticket_head, 1ull));
+        sm.w[0] = resolve_blocking<Tr>(a, g, none);
+        if (sm.w[0].kind == 1) issue_tile_load<Tr>(a, sm.w[0], sm, 0);
+    }
+    __syncthreads();
+    if (a.profile) tm[0] += clock64() - t_wait;
+    int b = 0;
+    if (sm.w[0].kind == 1 && sm.w[0].full) pending |= 1u;
+    bool aborted = false;
+    // The current work item lives in sm.w[0], the next one in sm.w[1].
+    while (sm.w[0].kind == 1) {
+        if (tid == 0) {
+            // Claim the next ticket now; prefetch its tile if its task is known.
+            const long long g = static_cast<long long>(atomicAdd(&a.ctrl->ticket_head, 1ull));
+            sm.next_ticket = g;
+            sm.w[1] = try_resolve<Tr>(a, g, sm.w[0]);
+            if (sm.w[1].kind == 1) issue_tile_load<Tr>(a, sm.w[1], sm, b ^ 1);
+        }
+        const int r = partition_tile<Tr>(a, sm.w[0], sm.w[1], sm, b, phases, tm);
+        pending &= ~(1u << b);
+        if (sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);  // written before the tile's barriers
+        if (r < 0) {
+            aborted = true;
+            break;
+        }
+        if (r == 1) {
+            const long long t6 = a.profile ? clock64() : 0;
+            finish_task<Tr>(a, sm.w[0], sm);
+            if (a.profile) tm[6] += clock64() - t6;
+        }
+        if (sm.w[1].kind == 0) {
+            const long long t0w = a.profile ? clock64() : 0;
+            __syncthreads();
+            if (tid == 0) {
+                sm.w[1] = resolve_blocking<Tr>(a, sm.next_ticket, sm.w[0]);
+                if (sm.w[1].kind == 1) issue_tile_load<Tr>(a, sm.w[1], sm, b ^ 1);
+            }
+            __syncthreads();
+            if (sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);
+            if (a.profile) tm[0] += clock64() - t0w;
+        }
+        __syncthreads();
+        if (tid == 0) sm.w[0] = sm.w[1];
+        __syncthreads();
+        b ^= 1;
+    }
+    // Never leave while a bulk copy may still be writing this CTA's shared memory.
+    for (int i = 0; i < 2; ++i)
+        if ((pending >> i) & 1u) mbar_wait_bounded(&sm.bar[i], (phases >> i) & 1u, a.ctrl, a.wait_limit_ns);
+    __syncthreads();
+    if (a.profile && tid == 0)
+        for (int i = 0; i < 8; ++i) atomicAdd(&a.ctrl->cycles[i], static_cast<unsigned long long>(tm[i]));
+    if (aborted) return;
+    // Clean exit: every task is finished, so no CTA reads the look-back words
+    // or the ticket owners any more; clear this CTA's share for the next call.
+    if (ld_relaxed_s32(&a.ctrl->status) == 0) {
+        const unsigned long long used = ld_relaxed_u64(&a.ctrl->pool_cursor);
+        const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * kThreads;
+        for (unsigned long long i = blockIdx.x * kThreads + tid; i < used; i += stride) {
+            a.pool[i] = 0;
+            a.owner[i] = 0;
+        }
+        if (tid == 0) atomicAdd(&a.ctrl->exited, 1ull);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Setup: one CTA resets the control block and seeds the root task.
+// ---------------------------------------------------------------------------
+template <class Tr>
+__global__ void __launch_bounds__(kThreads) setup_kernel(Args<typename Tr::K, typename Tr::V> a)
+{
+    using K = typename Tr::K;
+    __shared__ NewTask nt;
+    __shared__ int ok;
+    Ctrl *c = a.ctrl;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        c->ticket_head = 0;
+        c->n_tasks = c->pool_cursor = 0;
+        c->pending = 0;
+        c->n_large = c->n_small = 0;
+        c->claim_large = c->claim_small = 0;
+        c->status = 0;
+        c->info = 0;
+        c->part_tasks = c->part_keys = c->leaf_parts = c->leaf_keys = c->copy_keys = c->max_depth = 0;
+        c->lt_result = 0;
+        c->exited = 0;
+        for (int i = 0; i < 8; ++i) c->cycles[i] = 0;
+        ok = 0;
+        __threadfence();
+    }
+    __syncthreads();
+    if (a.partition_only || a.n > a.leaf_max) {
+        uint64_t pbits = a.pivot_bits;
+        if (!a.partition_only && tid < 32) pbits = sample_median<K>(a.keys[0], 0, a.n, 0x51ED5EEDull);
+        if (tid == 0) {
+            ok = alloc_task<Tr>(a, 0, a.n, 0, pbits, kModeLess, 0, nt);
+            if (ok) c->pending = 1;
+        }
+        __syncthreads();
+        if (ok) publish_task(a.owner, nt);
+    } else if (a.n > 1) {
+        if (tid == 0) push_leaf<Tr>(a, 0, a.n, 0);
+    }
+}
+
+}  // namespace qs

@@ -4,11 +4,16 @@
 //   Task   -- one device-wide partition of a range [off, off+len) of buffer
 //             `src` (0 = caller's array, 1 = scratch) around `pivot`; split
 //             into tiles that any CTA of the persistent kernel may claim.
-//   queue  -- FIFO of task ids (+1; 0 = slot reserved but not yet written).
 //   pool   -- look-back words, one per tile of every task (Merrill & Garland
 //             single-pass scan with decoupled look-back): 2 flag bits
 //             (aggregate available / inclusive prefix available) + 62-bit
-//             count of keys sent to the lower side.
+//             count of keys sent to the lower side.  A task's tiles own a
+//             contiguous range of words, reserved when the task is created;
+//             the word index doubles as the tile's global ticket.
+//   owner  -- for every ticket, the id (+1) of the task it belongs to
+//             (0 = not yet published).  CTAs claim tickets in increasing
+//             order with one atomic, so every wait (look-back, task
+//             completion) points to a lower ticket and cannot form a cycle.
 //   leaves -- parts left for the Bitonic kernel.  "Large" entries fill the
 //             array from the front (one CTA each), "small" ones from the back
 //             (one warp each).
@@ -58,7 +63,7 @@ constexpr int kLeafScratch = 1;
 constexpr int kLeafFinal = 2;
 
 struct alignas(128) Ctrl {
-    unsigned long long q_head, q_tail;
+    unsigned long long ticket_head;  // next ticket to hand out
     unsigned long long n_tasks, pool_cursor;
     long long pending;  // device-wide partition tasks created and not finished
     unsigned long long n_large, n_small;
@@ -68,6 +73,7 @@ struct alignas(128) Ctrl {
     unsigned long long part_tasks, part_keys, leaf_parts, leaf_keys, copy_keys, max_depth;
     unsigned long long lt_result;  // split index of a partition-only call
     unsigned long long exited;     // CTAs of the persistent kernel that left cleanly
+    unsigned long long cycles[8];  // per-phase SM cycles (profiling on)
 };
 
 // Arguments of the device kernels (passed by value).
@@ -79,16 +85,17 @@ struct Args {
     int val_vec[2];    // value buffer shares the key buffer's 16-byte phase
     int64_t n;
     Task *tasks;
-    int32_t *queue;
+    int32_t *owner;  // pool_cap entries
     unsigned long long *pool;
     Leaf *leaves;
     Ctrl *ctrl;
-    int64_t task_cap, pool_cap, leaf_cap;
+    int64_t task_cap, pool_cap, leaf_cap;  // owner and pool hold pool_cap entries
     int64_t leaf_max;   // parts up to this size go to the Bitonic kernel
     int64_t small_max;  // parts up to this size are sorted by one warp
     uint64_t wait_limit_ns;
     uint64_t pivot_bits;  // partition-only: the caller's pivot
     int partition_only;
+    int profile;  // accumulate per-phase cycle counts into ctrl->cycles
 };
 
 // Launch description computed by the host and consumed by the per-kind launchers.

@@ -1,11 +1,11 @@
 // Kernel instantiation and launcher for the "f64" element kind.
-#include "qs_kernels.cuh"
+#include "qs_launch.cuh"
 
 namespace qs {
 
 namespace {
-using Tr = Traits<double, false, 4, 4096, 512>;
-using L = Launcher<Tr, 4, 2>;
+using Tr = Traits<double, false, 8, 4096, 512>;
+using L = Launcher<Tr, 3, 2>;
 }  // namespace
 
 int launch_f64(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg) { return L::launch(a, cfg); }

@@ -1,11 +1,11 @@
 // Kernel instantiation and launcher for the "kv" element kind.
-#include "qs_kernels.cuh"
+#include "qs_launch.cuh"
 
 namespace qs {
 
 namespace {
 using Tr = Traits<int32_t, true, 4, 4096, 512>;
-using L = Launcher<Tr, 4, 2>;
+using L = Launcher<Tr, 3, 2>;
 }  // namespace
 
 int launch_kv(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg) { return L::launch(a, cfg); }

@@ -1,0 +1,66 @@
+// Host-side launcher of one element kind: setup kernel, persistent partition
+// kernel, leaf kernel, all on the caller's stream.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qs_driver.cuh"
+#include "qs_leaf.cuh"
+
+namespace qs {
+
+template <class Tr, int DriverMin, int LeafMin>
+struct Launcher {
+    using K = typename Tr::K;
+    using V = typename Tr::V;
+    static constexpr size_t kDriverSmem = sizeof(DriverSmem<Tr>);
+
+    static KernelLimits limits()
+    {
+        KernelLimits l;
+        l.leaf_max = Tr::LEAF;
+        l.small_max = Tr::SMALL;
+        l.tile = Tr::T;
+        l.driver_smem = kDriverSmem;
+        l.leaf_smem = sizeof(LeafSmem<Tr>);
+        return l;
+    }
+    static int prepare()
+    {
+        static int done = 0;
+        static int rc = 0;
+        if (!done) {
+            rc = cudaFuncSetAttribute(driver_kernel<Tr, DriverMin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(kDriverSmem));
+            done = 1;
+        }
+        return rc;
+    }
+    static int occ(int which, int *bps)
+    {
+        int rc = prepare();
+        if (rc) return rc;
+        if (which == 0)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, driver_kernel<Tr, DriverMin>, kThreads,
+                                                                 kDriverSmem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, leaf_kernel<Tr, LeafMin>, kThreads, 0);
+    }
+    static int launch(const Args<K, V> &a, LaunchCfg &cfg)
+    {
+        int rc = prepare();
+        if (rc) return rc;
+        cudaStream_t s = static_cast<cudaStream_t>(cfg.stream);
+        cudaEvent_t *ev = reinterpret_cast<cudaEvent_t *>(cfg.ev);
+        if (cfg.profile) cudaEventRecord(ev[0], s);
+        setup_kernel<Tr><<<1, kThreads, 0, s>>>(a);
+        if (cfg.profile) cudaEventRecord(ev[1], s);
+        if (a.partition_only || a.n > a.leaf_max)
+            driver_kernel<Tr, DriverMin><<<cfg.grid_driver, kThreads, kDriverSmem, s>>>(a);
+        if (cfg.profile) cudaEventRecord(ev[2], s);
+        if (!a.partition_only) leaf_kernel<Tr, LeafMin><<<cfg.grid_leaf, kThreads, 0, s>>>(a);
+        if (cfg.profile) cudaEventRecord(ev[3], s);
+        return static_cast<int>(cudaGetLastError());
+    }
+};
+
+}  // namespace qs
