@@ -388,14 +388,12 @@ int run_host(int kind, K *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream
 }
 
 uint64_t bits_i32(int32_t k) { return static_cast<uint64_t>(static_cast<int64_t>(k)); }
-// The kernels compare doubles in sort space: the IEEE bits with the sign bit
-// flipped for non-negative values and every bit flipped for negative ones.
 uint64_t bits_f64(double k)
 {
     if (k == 0.0) k = 0.0;  // a -0.0 pivot splits exactly like +0.0
     uint64_t b;
     std::memcpy(&b, &k, 8);
-    return b ^ (static_cast<uint64_t>(static_cast<int64_t>(b) >> 63) | 0x8000000000000000ull);
+    return b;
 }
 
 }  // namespace

@@ -24,11 +24,22 @@ namespace qs {
 template <class K>
 struct KeyOps;
 
+// The partition compares raw keys against the pivot: int32 as signed
+// integers; doubles through their IEEE bits as 64-bit integers -- signed
+// compare when the pivot is non-negative, unsigned compare with the direction
+// reversed when it is negative (no NaN, no -0.0 among the keys).  The leaf
+// sort uses the sort-space map below instead.
 template <>
 struct KeyOps<int32_t> {
     using S = int32_t;
+    using Raw = int32_t;
+    using URaw = uint32_t;
     using Vec = int4;
     static constexpr int VW = 4;  // keys per 16-byte vector
+    static constexpr bool kSigned = false;  // no sign-dependent compare needed
+    __device__ __forceinline__ static Raw raw(int32_t k) { return k; }
+    __device__ __forceinline__ static Raw raw_from_bits(uint64_t b) { return static_cast<int32_t>(static_cast<int64_t>(b)); }
+    __device__ __forceinline__ static uint64_t to_bits(int32_t k) { return static_cast<uint64_t>(static_cast<int64_t>(k)); }
     __device__ __forceinline__ static S to_s(int32_t k) { return k; }
     __device__ __forceinline__ static int32_t from_s(S s) { return s; }
     __device__ __forceinline__ static S s_largest() { return 0x7fffffff; }
@@ -46,8 +57,14 @@ struct KeyOps<int32_t> {
 template <>
 struct KeyOps<double> {
     using S = unsigned long long;
+    using Raw = long long;
+    using URaw = unsigned long long;
     using Vec = double2;
     static constexpr int VW = 2;
+    static constexpr bool kSigned = true;
+    __device__ __forceinline__ static Raw raw(double k) { return __double_as_longlong(k); }
+    __device__ __forceinline__ static Raw raw_from_bits(uint64_t b) { return static_cast<long long>(b); }
+    __device__ __forceinline__ static uint64_t to_bits(double k) { return static_cast<uint64_t>(__double_as_longlong(k)); }
     __device__ __forceinline__ static S to_s(double k)
     {
         const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(k));
@@ -67,6 +84,19 @@ struct KeyOps<double> {
         o[1] = v.y;
     }
 };
+
+// Does a key (raw) go to the lower side?  LE selects '<=' (the equal-key
+// pass), NEG a negative double pivot (unsigned, reversed compare).
+template <class Ops, bool LE, bool NEG>
+__device__ __forceinline__ bool goes_low(typename Ops::Raw k, typename Ops::Raw p)
+{
+    using U = typename Ops::URaw;
+    if constexpr (NEG) {
+        return LE ? static_cast<U>(k) >= static_cast<U>(p) : static_cast<U>(k) > static_cast<U>(p);
+    } else {
+        return LE ? k <= p : k < p;
+    }
+}
 
 // Compile-time configuration of one element kind.
 //   VPT   16-byte vectors per thread per partition tile

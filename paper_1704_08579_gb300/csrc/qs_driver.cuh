@@ -34,7 +34,7 @@ namespace qs {
 // Pivot selection.  The paper's experiments use a median of three values
 // (Section IV-A); here the median of 64 keys sampled at jittered strides over
 // the range, sorted by one warp with the Bitonic network.  Called by a full
-// warp; returns the pivot in sort space, as bits.
+// warp; returns the pivot's raw bits (int32 sign-extended, or IEEE bits).
 // ---------------------------------------------------------------------------
 template <class K>
 __device__ uint64_t sample_median(const K *src, int64_t off, int64_t len, uint64_t salt)
@@ -53,7 +53,7 @@ __device__ uint64_t sample_median(const K *src, int64_t off, int64_t len, uint64
         s[r] = Ops::to_s(__ldcg(src + off + (static_cast<int64_t>(i) * len) / 64 + jitter));
     }
     warp_bitonic_sort<2, S, int32_t, false>(s, dummy);
-    return Ops::s_to_bits(__shfl_sync(0xffffffffu, s[0], 16));  // element 32 of 64
+    return Ops::to_bits(Ops::from_s(__shfl_sync(0xffffffffu, s[0], 16)));  // element 32 of 64, raw bits
 }
 
 // ---------------------------------------------------------------------------
@@ -184,6 +184,7 @@ struct DriverSmem {
     int low_total;
     int eq_total;
     int next_low;  // early count of the prefetched tile (warps 1..7)
+    long long tm[8];  // per-phase cycles (thread 0, profiling on)
     int last;
     int abort;
     WorkItem w[2];  // [0] current, [1] next
@@ -340,6 +341,67 @@ static __device__ long long lookback(unsigned long long *words, int tile, unsign
 }
 
 // ---------------------------------------------------------------------------
+// Compare helpers, instantiated for '<' / '<=' and for the sign of a double
+// pivot so that the per-key work is one integer compare.
+// ---------------------------------------------------------------------------
+template <class Tr, bool LE, bool NEG>
+__device__ __forceinline__ uint32_t low_mask(const typename Tr::K (&key)[Tr::E], typename KeyOps<typename Tr::K>::Raw p,
+                                             uint32_t validm, int &eq)
+{
+    using Ops = KeyOps<typename Tr::K>;
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < Tr::E; ++i) {
+        const typename Ops::Raw k = Ops::raw(key[i]);
+        m |= goes_low<Ops, LE, NEG>(k, p) ? (1u << i) : 0u;
+        eq += ((validm >> i) & 1u) && k == p ? 1 : 0;
+    }
+    return m & validm;
+}
+
+template <class Tr, bool LE, bool NEG>
+__device__ __forceinline__ int count_low(const typename Tr::K *buf, typename KeyOps<typename Tr::K>::Raw p)
+{
+    using Ops = KeyOps<typename Tr::K>;
+    using Vec = typename Ops::Vec;
+    constexpr int NV = Tr::T / Tr::VW;
+    const Vec *v = reinterpret_cast<const Vec *>(buf);
+    int cnt = 0;
+    for (int i = threadIdx.x - 32; i < NV; i += kThreads - 32) {
+        typename Tr::K tmp[Tr::VW];
+        Ops::split(v[i], tmp);
+#pragma unroll
+        for (int j = 0; j < Tr::VW; ++j) cnt += goes_low<Ops, LE, NEG>(Ops::raw(tmp[j]), p) ? 1 : 0;
+    }
+    return cnt;
+}
+
+template <class Tr>
+__device__ __forceinline__ uint32_t low_mask_any(const typename Tr::K (&key)[Tr::E], uint64_t pivot_bits, int mode,
+                                                 uint32_t validm, int &eq)
+{
+    using Ops = KeyOps<typename Tr::K>;
+    const typename Ops::Raw p = Ops::raw_from_bits(pivot_bits);
+    const bool le = mode == kModeLessEqual;
+    if constexpr (Ops::kSigned) {
+        if (p < 0) return le ? low_mask<Tr, true, true>(key, p, validm, eq) : low_mask<Tr, false, true>(key, p, validm, eq);
+    }
+    return le ? low_mask<Tr, true, false>(key, p, validm, eq) : low_mask<Tr, false, false>(key, p, validm, eq);
+}
+
+template <class Tr>
+__device__ __forceinline__ int count_low_any(const typename Tr::K *buf, uint64_t pivot_bits, int mode)
+{
+    using Ops = KeyOps<typename Tr::K>;
+    const typename Ops::Raw p = Ops::raw_from_bits(pivot_bits);
+    const bool le = mode == kModeLessEqual;
+    if constexpr (Ops::kSigned) {
+        if (p < 0) return le ? count_low<Tr, true, true>(buf, p) : count_low<Tr, false, true>(buf, p);
+    }
+    return le ? count_low<Tr, true, false>(buf, p) : count_low<Tr, false, false>(buf, p);
+}
+
+// ---------------------------------------------------------------------------
 // One partition tile.  Vector k of thread t covers tile positions
 // k*NT*VW + t*VW + j, so the input order is (k, warp, lane, j).  The pivot
 // compare (the paper's vector compare into a mask) becomes warp ballots whose
@@ -351,12 +413,11 @@ static __device__ long long lookback(unsigned long long *words, int tile, unsign
 // ---------------------------------------------------------------------------
 template <class Tr>
 __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, const WorkItem &w, WorkItem &nx,
-                              DriverSmem<Tr> &sm, int b, uint32_t &phases, long long *tm)
+                              DriverSmem<Tr> &sm, int b, uint32_t &phases)
 {
     using K = typename Tr::K;
     using V = typename Tr::V;
     using Ops = KeyOps<K>;
-    using S = typename Ops::S;
     using Vec = typename Ops::Vec;
     constexpr int VW = Tr::VW, VPT = Tr::VPT, T = Tr::T, E = Tr::E;
     constexpr int NC = VPT * kWarps;       // (vector, warp) chunk counts
@@ -364,24 +425,20 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    K *__restrict__ dk = a.keys[w.src ^ 1];
-    V *__restrict__ dv = a.vals[w.src ^ 1];
     const int64_t off = w.off, end = w.off + w.len;
     const int64_t base = w.w0 + static_cast<int64_t>(w.tile) * T;
-    const S pivot = Ops::s_from_bits(w.pivot);
-    const bool le = w.mode == kModeLessEqual;
+
+    long long tprev = (a.profile && tid == 0) ? clock64() : 0;
+#define QS_TICK(slot)                         \
+    if (a.profile && tid == 0) {              \
+        const long long tnow_ = clock64();    \
+        sm.tm[slot] += tnow_ - tprev;         \
+        tprev = tnow_;                        \
+    }
 
     K key[E];
     V val[Tr::KV ? E : 1];
-    uint32_t lowm = 0, validm = 0;
-
-    long long tprev = a.profile ? clock64() : 0;
-#define QS_TICK(slot)                         \
-    if (a.profile) {                          \
-        const long long tnow_ = clock64();    \
-        tm[slot] += tnow_ - tprev;            \
-        tprev = tnow_;                        \
-    }
+    uint32_t validm = 0;
     if (w.full) {
         if (!mbar_wait_bounded(&sm.bar[b], (phases >> b) & 1u, a.ctrl, a.wait_limit_ns)) return -1;
         phases ^= 1u << b;
@@ -419,14 +476,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         }
     }
     int eq = 0;
-#pragma unroll
-    for (int i = 0; i < E; ++i) {
-        const S s = Ops::to_s(key[i]);
-        const bool v = (validm >> i) & 1u;
-        const bool lo = v && (le ? !(pivot < s) : s < pivot);
-        lowm |= lo ? (1u << i) : 0u;
-        eq += (v && s == pivot) ? 1 : 0;
-    }
+    const uint32_t lowm = low_mask_any<Tr>(key, w.pivot, w.mode, validm, eq);
 
     // Warp ballots -> rank of each key among the lower-side keys of its (k, warp) chunk.
     int rank[VPT];
@@ -486,14 +536,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         // aggregate at once, so tiles after it never wait for this CTA to
         // finish the current tile.
         if (mbar_wait_bounded(&sm.bar[b ^ 1], (phases >> (b ^ 1)) & 1u, a.ctrl, a.wait_limit_ns)) {
-            const S npiv = Ops::s_from_bits(nx.pivot);
-            const bool nle = nx.mode == kModeLessEqual;
-            const K *nk = sm.kbuf[b ^ 1];
-            int cnt = 0;
-            for (int i = tid - 32; i < T; i += kThreads - 32) {
-                const S s = Ops::to_s(nk[i]);
-                cnt += (nle ? !(npiv < s) : s < npiv) ? 1 : 0;
-            }
+            int cnt = count_low_any<Tr>(sm.kbuf[b ^ 1], nx.pivot, nx.mode);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
             if (lane == 0) atomicAdd(&sm.next_low, cnt);
@@ -515,6 +558,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     const int64_t vstart = base > off ? base : off;
     const int64_t vend = base + T < end ? base + T : end;
     const int nvalid = static_cast<int>(vend - vstart);
+    const int vofs = static_cast<int>(vstart - base);  // window slots before the first valid key
     K *stage_k = sm.kbuf[b];
     V *stage_v = sm.vbuf[b];
 
@@ -522,14 +566,13 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
         int r = sm.wcount[k * kWarps + warp] + rank[k];
-        const int64_t e = base + static_cast<int64_t>(k) * kThreads * VW + tid * VW;
+        const int e = k * kThreads * VW + tid * VW - vofs;
 #pragma unroll
         for (int j = 0; j < VW; ++j) {
             const int i = k * VW + j;
             const bool lo = (lowm >> i) & 1u;
             if ((validm >> i) & 1u) {
-                const int q = static_cast<int>(e + j - vstart);  // position among valid keys
-                const int s = lo ? r : L + (q - r);
+                const int s = lo ? r : L + (e + j - r);
                 stage_k[s] = key[i];
                 if constexpr (Tr::KV) stage_v[s] = val[i];
             }
@@ -538,18 +581,23 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     }
     __syncthreads();
 
-    const int64_t hpre = (vstart - off) - excl;  // upper-side keys in earlier tiles
-    bool bad = false;
-    for (int s = tid; s < nvalid; s += kThreads) {
-        const int64_t d = s < L ? off + excl + s : end - 1 - (hpre + (s - L));
-        if (d < off || d >= end) {  // never taken when the scan is consistent
-            bad = true;
-            continue;
+    // Lower side: [off + excl, +L); upper side (reverse order) ends at
+    // end - 1 - hpre, where hpre = upper-side keys of the earlier tiles.
+    const int64_t hpre = (vstart - off) - excl;
+    const int H = nvalid - L;
+    if (excl >= 0 && off + excl + L <= end && hpre >= 0 && hpre + H <= w.len) {
+        K *__restrict__ lo_k = a.keys[w.src ^ 1] + (off + excl);
+        K *__restrict__ hi_k = a.keys[w.src ^ 1] + (end - 1 - hpre + L);  // key s >= L goes to hi_k - s
+        V *__restrict__ lo_v = a.vals[w.src ^ 1] + (off + excl);
+        V *__restrict__ hi_v = a.vals[w.src ^ 1] + (end - 1 - hpre + L);
+        for (int s = tid; s < nvalid; s += kThreads) {
+            const bool lo = s < L;
+            *(lo ? lo_k + s : hi_k - s) = stage_k[s];
+            if constexpr (Tr::KV) *(lo ? lo_v + s : hi_v - s) = stage_v[s];
         }
-        dk[d] = stage_k[s];
-        if constexpr (Tr::KV) dv[d] = stage_v[s];
+    } else if (tid == 0) {
+        set_error(a.ctrl, kErrInternalIndex, 1);  // never taken when the scan is consistent
     }
-    if (bad) set_error(a.ctrl, kErrInternalIndex, 1);
     __syncthreads();
     QS_TICK(4);
     if (tid == 0) {
@@ -584,7 +632,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     __syncthreads();
     QS_TICK(5);
 #undef QS_TICK
-    tm[7] += 1;
+    if (a.profile && tid == 0) sm.tm[7] += 1;
     return sm.last;
 }
 
@@ -714,9 +762,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
     const int tid = threadIdx.x;
     uint32_t phases = 0;   // bit b: parity of the next completion of bar[b]
     uint32_t pending = 0;  // bit b: a bulk load into buffer b is issued and not yet consumed
-    long long tm[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per-phase cycles (thread 0, profiling on)
     long long t_wait = a.profile ? clock64() : 0;
     if (tid == 0) {
+        for (int i = 0; i < 8; ++i) sm.tm[i] = 0;
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
         fence_mbar_init();
@@ -729,7 +777,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
         if (sm.w[0].kind == 1) issue_tile_load<Tr>(a, sm.w[0], sm, 0);
     }
     __syncthreads();
-    if (a.profile) tm[0] += clock64() - t_wait;
+    if (a.profile && tid == 0) sm.tm[0] += clock64() - t_wait;
     int b = 0;
     if (sm.w[0].kind == 1 && sm.w[0].full) pending |= 1u;
     bool aborted = false;
@@ -742,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
             sm.w[1] = try_resolve<Tr>(a, g, sm.w[0]);
             if (sm.w[1].kind == 1) issue_tile_load<Tr>(a, sm.w[1], sm, b ^ 1);
         }
-        const int r = partition_tile<Tr>(a, sm.w[0], sm.w[1], sm, b, phases, tm);
+        const int r = partition_tile<Tr>(a, sm.w[0], sm.w[1], sm, b, phases);
         pending &= ~(1u << b);
         if (sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);  // written before the tile's barriers
         if (r < 0) {
@@ -752,7 +800,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
         if (r == 1) {
             const long long t6 = a.profile ? clock64() : 0;
             finish_task<Tr>(a, sm.w[0], sm);
-            if (a.profile) tm[6] += clock64() - t6;
+            if (a.profile && tid == 0) sm.tm[6] += clock64() - t6;
         }
         if (sm.w[1].kind == 0) {
             const long long t0w = a.profile ? clock64() : 0;
@@ -763,7 +811,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
             }
             __syncthreads();
             if (sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);
-            if (a.profile) tm[0] += clock64() - t0w;
+            if (a.profile && tid == 0) sm.tm[0] += clock64() - t0w;
         }
         __syncthreads();
         if (tid == 0) sm.w[0] = sm.w[1];
@@ -775,7 +823,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
         if ((pending >> i) & 1u) mbar_wait_bounded(&sm.bar[i], (phases >> i) & 1u, a.ctrl, a.wait_limit_ns);
     __syncthreads();
     if (a.profile && tid == 0)
-        for (int i = 0; i < 8; ++i) atomicAdd(&a.ctrl->cycles[i], static_cast<unsigned long long>(tm[i]));
+        for (int i = 0; i < 8; ++i) atomicAdd(&a.ctrl->cycles[i], static_cast<unsigned long long>(sm.tm[i]));
     if (aborted) return;
     // Clean exit: every task is finished, so no CTA reads the look-back words
     // or the ticket owners any more; clear this CTA's share for the next call.
