@@ -9,21 +9,21 @@
 // Algorithm 1's six stages are exactly s=2: xor 1; s=4: xor 3, xor 1;
 // s=8: xor 7, xor 2, xor 1.
 //
-// Here the same network runs on a GPU with the rule-based indexing the paper
-// mentions as the alternative to hard-coded tables (Section II-A-3):
+// Here the same network runs with the rule-based indexing the paper mentions
+// as the alternative to hard-coded tables (Section II-A-3):
 //   * element i = t*E + r lives in register r of thread t (blocked layout);
-//   * a stage whose partner is in the same thread is a register min/max;
+//   * a stage whose partner is in the same thread is a register min/max,
+//     generated at compile time (it does not depend on the block size);
 //   * a stage whose partner is in another lane of the warp uses
-//     __shfl_xor_sync (the GPU counterpart of the paper's permutexvar);
-//   * a stage whose partner is in another warp goes through shared memory.
+//     __shfl_xor_sync (the GPU counterpart of the paper's permutexvar), in a
+//     run-time loop over block sizes so the code stays small;
+//   * a stage whose partner is in another warp runs in shared memory.
 // Because every comparator sends the minimum to the lower index, padding the
 // tail with the largest key (Section III-A-3) never moves: a pad only meets
-// elements at lower indices, and a real key never compares greater than the
-// largest key.  This also keeps key/value pads from ever swapping with a real
-// pair whose key equals the pad.
-//
-// Key/value (Section III-D): the comparison looks at keys only and the value
-// moves with its key.
+// elements at lower indices, and no key compares greater than the largest
+// key.  Keys are compared as integers ("sort space"); key/value pairs are
+// packed into one 64-bit word with the key in the high half (Section III-D:
+// the value moves with its key).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -31,109 +31,81 @@
 
 namespace qs {
 
-template <class K>
-__device__ __forceinline__ bool key_less(K a, K b)
+// (a, b) -> (min, max); equal keys stay put.
+template <class S>
+__device__ __forceinline__ void cx(S &a, S &b)
 {
-    return a < b;
-}
-
-// Compare-exchange of two registers of one thread: (a, b) -> (min, max).
-template <class K, class V, bool KV>
-__device__ __forceinline__ void cmpx(K &a, K &b, V &va, V &vb)
-{
-    const bool swap = key_less(b, a);
-    const K lo = swap ? b : a;
-    const K hi = swap ? a : b;
+    const bool sw = b < a;
+    const S lo = sw ? b : a;
+    b = sw ? a : b;
     a = lo;
-    b = hi;
-    if constexpr (KV) {
-        const V vlo = swap ? vb : va;
-        const V vhi = swap ? va : vb;
-        va = vlo;
-        vb = vhi;
-    }
 }
 
-// Blocked layout inside one warp: E registers per lane, 32*E elements.
-// Flip stage of block size s: partner i ^ (s-1).
-template <int E, int S, class K, class V, bool KV>
-__device__ __forceinline__ void flip_stage_warp(K (&k)[E], V (&v)[E], int lane)
-{
-    if constexpr (S <= E) {
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const int p = r ^ (S - 1);
-            if (r < p) cmpx<K, V, KV>(k[r], k[p], v[r], v[p]);
-        }
-    } else {
-        constexpr int kLaneMask = S / E - 1;  // partner lane = lane ^ kLaneMask
-        const bool lower = (lane & (S / E / 2)) == 0;
-        K rk[E];
-        V rv[E];
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            rk[r] = __shfl_xor_sync(0xffffffffu, k[E - 1 - r], kLaneMask);
-            if constexpr (KV) rv[r] = __shfl_xor_sync(0xffffffffu, v[E - 1 - r], kLaneMask);
-        }
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const bool take = lower ? key_less(rk[r], k[r]) : key_less(k[r], rk[r]);
-            k[r] = take ? rk[r] : k[r];
-            if constexpr (KV) v[r] = take ? rv[r] : v[r];
-        }
-    }
-}
-
-// Half-cleaner stage: partner i ^ J.
-template <int E, int J, class K, class V, bool KV>
-__device__ __forceinline__ void half_stage_warp(K (&k)[E], V (&v)[E], int lane)
-{
-    if constexpr (J < E) {
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            if ((r & J) == 0) cmpx<K, V, KV>(k[r], k[r | J], v[r], v[r | J]);
-        }
-    } else {
-        constexpr int kLaneMask = J / E;
-        const bool lower = (lane & kLaneMask) == 0;
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const K o = __shfl_xor_sync(0xffffffffu, k[r], kLaneMask);
-            V ov{};
-            if constexpr (KV) ov = __shfl_xor_sync(0xffffffffu, v[r], kLaneMask);
-            const bool take = lower ? key_less(o, k[r]) : key_less(k[r], o);
-            k[r] = take ? o : k[r];
-            if constexpr (KV) v[r] = take ? ov : v[r];
-        }
-    }
-}
-
-// Half-cleaners J, J/2, ..., 1 (compile-time recursion keeps indices static).
-template <int E, int J, class K, class V, bool KV>
-__device__ __forceinline__ void half_cleaners_warp(K (&k)[E], V (&v)[E], int lane)
+// Half-cleaners J, J/2, ..., 1 inside one thread's registers.
+template <int E, int J, class S>
+__device__ __forceinline__ void reg_half(S (&k)[E])
 {
     if constexpr (J >= 1) {
-        half_stage_warp<E, J, K, V, KV>(k, v, lane);
-        half_cleaners_warp<E, J / 2, K, V, KV>(k, v, lane);
+#pragma unroll
+        for (int r = 0; r < E; ++r)
+            if ((r & J) == 0) cx(k[r], k[r | J]);
+        reg_half<E, J / 2>(k);
     }
 }
 
-// Merge steps for block sizes S, 2S, ..., SMAX, all inside one warp.
-template <int E, int S, int SMAX, class K, class V, bool KV>
-__device__ __forceinline__ void merges_warp(K (&k)[E], V (&v)[E], int lane)
+// Merge steps for block sizes SZ, 2*SZ, ..., E inside one thread.
+template <int E, int SZ, class S>
+__device__ __forceinline__ void reg_merges(S (&k)[E])
 {
-    if constexpr (S <= SMAX) {
-        flip_stage_warp<E, S, K, V, KV>(k, v, lane);
-        half_cleaners_warp<E, S / 4, K, V, KV>(k, v, lane);
-        merges_warp<E, S * 2, SMAX, K, V, KV>(k, v, lane);
+    if constexpr (SZ <= E) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int p = r ^ (SZ - 1);
+            if (r < p) cx(k[r], k[p]);
+        }
+        reg_half<E, SZ / 4>(k);
+        reg_merges<E, SZ * 2, S>(k);
+    }
+}
+
+// Flip stage across lanes: lane l pairs with l ^ lm, register r with E-1-r.
+// `upper` is true on the lane holding the higher indices (keeps the maximum).
+template <int E, class S>
+__device__ __forceinline__ void shfl_flip(S (&k)[E], int lm, bool upper)
+{
+    S o[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) o[r] = __shfl_xor_sync(0xffffffffu, k[E - 1 - r], lm);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const bool take = upper ? (k[r] < o[r]) : (o[r] < k[r]);
+        k[r] = take ? o[r] : k[r];
+    }
+}
+
+// Half-cleaner across lanes: lane l pairs with l ^ m, same register.
+template <int E, class S>
+__device__ __forceinline__ void shfl_half(S (&k)[E], int m, bool upper)
+{
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const S o = __shfl_xor_sync(0xffffffffu, k[r], m);
+        const bool take = upper ? (k[r] < o) : (o < k[r]);
+        k[r] = take ? o : k[r];
     }
 }
 
 // Sorts the 32*E elements held by one warp (blocked layout).
-template <int E, class K, class V, bool KV>
-__device__ __forceinline__ void warp_bitonic_sort(K (&k)[E], V (&v)[E])
+template <int E, class S>
+__device__ __forceinline__ void warp_bitonic_sort(S (&k)[E])
 {
-    merges_warp<E, 2, 32 * E, K, V, KV>(k, v, threadIdx.x & 31);
+    const int lane = threadIdx.x & 31;
+    reg_merges<E, 2, S>(k);
+    for (int sz = 2 * E; sz <= 32 * E; sz <<= 1) {
+        shfl_flip<E, S>(k, sz / E - 1, (lane & (sz / E / 2)) != 0);
+        for (int j = sz / 4; j >= E; j >>= 1) shfl_half<E, S>(k, j / E, (lane & (j / E)) != 0);
+        reg_half<E, E / 2>(k);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -143,97 +115,79 @@ __device__ __forceinline__ void warp_bitonic_sort(K (&k)[E], V (&v)[E])
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
 
-template <int NT, int E, class K, class V, bool KV>
-__device__ __forceinline__ void regs_to_smem(const K (&k)[E], const V (&v)[E], K *sk, V *sv)
+template <int E, class S>
+__device__ __forceinline__ void regs_to_smem(const S (&k)[E], S *sk)
 {
     const int base = threadIdx.x * E;
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        sk[pad32(base + r)] = k[r];
-        if constexpr (KV) sv[pad32(base + r)] = v[r];
-    }
+    for (int r = 0; r < E; ++r) sk[pad32(base + r)] = k[r];
 }
 
-template <int NT, int E, class K, class V, bool KV>
-__device__ __forceinline__ void smem_to_regs(K (&k)[E], V (&v)[E], const K *sk, const V *sv)
+template <int E, class S>
+__device__ __forceinline__ void smem_to_regs(S (&k)[E], const S *sk)
 {
     const int base = threadIdx.x * E;
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        k[r] = sk[pad32(base + r)];
-        if constexpr (KV) v[r] = sv[pad32(base + r)];
-    }
+    for (int r = 0; r < E; ++r) k[r] = sk[pad32(base + r)];
 }
 
-template <class K, class V, bool KV>
-__device__ __forceinline__ void smem_cmpx(K *sk, V *sv, int lo, int hi)
+template <class S>
+__device__ __forceinline__ void smem_cx(S *sk, int lo, int hi)
 {
     const int a = pad32(lo), b = pad32(hi);
-    K ka = sk[a], kb = sk[b];
-    if (key_less(kb, ka)) {
-        sk[a] = kb;
-        sk[b] = ka;
-        if constexpr (KV) {
-            V t = sv[a];
-            sv[a] = sv[b];
-            sv[b] = t;
-        }
-    }
+    S x = sk[a], y = sk[b];
+    cx(x, y);
+    sk[a] = x;
+    sk[b] = y;
 }
 
-// One flip stage (block size s) over P elements in shared memory.
-template <int NT, int P, class K, class V, bool KV>
-__device__ __forceinline__ void smem_flip(K *sk, V *sv, int s)
+// Flip stage of block size 2^(lh+1) over P elements in shared memory.
+template <int NT, int P, class S>
+__device__ __forceinline__ void smem_flip(S *sk, int lh)
 {
-    const int half = s >> 1;
+    const int half = 1 << lh;
+#pragma unroll 4
     for (int c = threadIdx.x; c < P / 2; c += NT) {
-        const int blk = c / half, w = c - blk * half;
-        smem_cmpx<K, V, KV>(sk, sv, blk * s + w, blk * s + s - 1 - w);
+        const int blk = c >> lh, w = c & (half - 1);
+        const int b0 = blk << (lh + 1);
+        smem_cx(sk, b0 + w, b0 + 2 * half - 1 - w);
     }
 }
 
-template <int NT, int P, class K, class V, bool KV>
-__device__ __forceinline__ void smem_half(K *sk, V *sv, int j)
+// Half-cleaner with partner distance 2^lj.
+template <int NT, int P, class S>
+__device__ __forceinline__ void smem_half(S *sk, int lj)
 {
+    const int j = 1 << lj;
+#pragma unroll 4
     for (int c = threadIdx.x; c < P / 2; c += NT) {
-        const int blk = c / j, w = c - blk * j;
-        const int lo = blk * 2 * j + w;
-        smem_cmpx<K, V, KV>(sk, sv, lo, lo + j);
+        const int lo = ((c >> lj) << (lj + 1)) + (c & (j - 1));
+        smem_cx(sk, lo, lo + j);
     }
 }
 
-template <int NT, int E, int S, class K, class V, bool KV>
-__device__ __forceinline__ void merges_cta(K (&k)[E], V (&v)[E], K *sk, V *sv)
+// Sorts NT*E elements held by the CTA (blocked layout); sk holds at least
+// pad32(NT*E) elements.
+template <int NT, int E, class S>
+__device__ __forceinline__ void cta_bitonic_sort(S (&k)[E], S *sk)
 {
     constexpr int P = NT * E;
-    if constexpr (S <= P) {
-        const int lane = threadIdx.x & 31;
-        if constexpr (S <= 32 * E) {
-            flip_stage_warp<E, S, K, V, KV>(k, v, lane);
-            half_cleaners_warp<E, S / 4, K, V, KV>(k, v, lane);
-        } else {
-            regs_to_smem<NT, E, K, V, KV>(k, v, sk, sv);
+    const int lane = threadIdx.x & 31;
+    warp_bitonic_sort<E, S>(k);
+    for (int sz = 64 * E, lg = __ffs(64 * E) - 1; sz <= P; sz <<= 1, ++lg) {  // lg = log2(sz)
+        regs_to_smem<E, S>(k, sk);
+        __syncthreads();
+        smem_flip<NT, P, S>(sk, lg - 1);
+        __syncthreads();
+        for (int lj = lg - 2; (1 << lj) >= 32 * E; --lj) {
+            smem_half<NT, P, S>(sk, lj);
             __syncthreads();
-            smem_flip<NT, P, K, V, KV>(sk, sv, S);
-            __syncthreads();
-            for (int j = S / 4; j >= 32 * E; j >>= 1) {
-                smem_half<NT, P, K, V, KV>(sk, sv, j);
-                __syncthreads();
-            }
-            smem_to_regs<NT, E, K, V, KV>(k, v, sk, sv);
-            __syncthreads();
-            half_cleaners_warp<E, 16 * E, K, V, KV>(k, v, lane);
         }
-        merges_cta<NT, E, S * 2, K, V, KV>(k, v, sk, sv);
+        smem_to_regs<E, S>(k, sk);
+        __syncthreads();
+        for (int j = 16 * E; j >= E; j >>= 1) shfl_half<E, S>(k, j / E, (lane & (j / E)) != 0);
+        reg_half<E, E / 2>(k);
     }
-}
-
-// Sorts NT*E elements held by the CTA (blocked layout); sk/sv hold at least
-// pad32(NT*E) elements.
-template <int NT, int E, class K, class V, bool KV>
-__device__ __forceinline__ void cta_bitonic_sort(K (&k)[E], V (&v)[E], K *sk, V *sv)
-{
-    merges_cta<NT, E, 2, K, V, KV>(k, v, sk, sv);
 }
 
 }  // namespace qs

@@ -43,7 +43,6 @@ __device__ uint64_t sample_median(const K *src, int64_t off, int64_t len, uint64
     using S = typename Ops::S;
     const int lane = threadIdx.x & 31;
     S s[2];
-    int32_t dummy[2] = {0, 0};
     const int64_t stride = len / 64;  // len > 64 for every partition task
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
@@ -52,7 +51,7 @@ __device__ uint64_t sample_median(const K *src, int64_t off, int64_t len, uint64
         const int64_t jitter = static_cast<int64_t>(h % static_cast<uint64_t>(stride > 0 ? stride : 1));
         s[r] = Ops::to_s(__ldcg(src + off + (static_cast<int64_t>(i) * len) / 64 + jitter));
     }
-    warp_bitonic_sort<2, S, int32_t, false>(s, dummy);
+    warp_bitonic_sort<2, S>(s);
     return Ops::to_bits(Ops::from_s(__shfl_sync(0xffffffffu, s[0], 16)));  // element 32 of 64, raw bits
 }
 

@@ -6,15 +6,51 @@
 // tail of a part is padded with the largest sort-space key (Section III-A-3).
 #pragma once
 
+#include <type_traits>
+
 #include "qs_bitonic.cuh"
 #include "qs_common.cuh"
 
 namespace qs {
 
+// Sort-space element of the leaf network: the integer image of a key
+// (KeyOps::to_s), or for key/value pairs the key in the high 32 bits and the
+// value's bits in the low 32 bits, compared as a signed 64-bit integer.
+template <class Tr>
+struct LeafKey {
+    using K = typename Tr::K;
+    using V = typename Tr::V;
+    using Ops = KeyOps<K>;
+    using S = typename std::conditional<Tr::KV, long long, typename Ops::S>::type;
+    __device__ __forceinline__ static S load(const K *gk, const V *gv, int i)
+    {
+        if constexpr (Tr::KV)
+            return static_cast<long long>((static_cast<unsigned long long>(static_cast<uint32_t>(gk[i])) << 32) |
+                                          static_cast<unsigned long long>(static_cast<uint32_t>(gv[i])));
+        else
+            return Ops::to_s(gk[i]);
+    }
+    __device__ __forceinline__ static void store(K *ok, V *ov, int i, S s)
+    {
+        if constexpr (Tr::KV) {
+            ok[i] = static_cast<int32_t>(static_cast<uint32_t>(static_cast<unsigned long long>(s) >> 32));
+            ov[i] = static_cast<int32_t>(static_cast<uint32_t>(static_cast<unsigned long long>(s)));
+        } else {
+            ok[i] = Ops::from_s(s);
+        }
+    }
+    __device__ __forceinline__ static S largest()
+    {
+        if constexpr (Tr::KV)
+            return 0x7fffffffffffffffll;
+        else
+            return Ops::s_largest();
+    }
+};
+
 template <class Tr>
 struct LeafSmem {
-    typename Tr::S keys[Tr::LEAF + Tr::LEAF / 32];
-    typename Tr::V vals[Tr::KV ? Tr::LEAF + Tr::LEAF / 32 : 1];
+    typename LeafKey<Tr>::S keys[Tr::LEAF + Tr::LEAF / 32];
     Leaf leaf;
     long long idx;
 };
@@ -32,68 +68,51 @@ __device__ bool leaf_ok(const Args<typename Tr::K, typename Tr::V> &a, const Lea
 template <class Tr, int E>
 __device__ void cta_leaf(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l, LeafSmem<Tr> &sm)
 {
-    using K = typename Tr::K;
-    using V = typename Tr::V;
-    using Ops = KeyOps<K>;
-    using S = typename Ops::S;
+    using LK = LeafKey<Tr>;
+    using S = typename LK::S;
     constexpr int P = kThreads * E;
     const int src = (l.flags & kLeafScratch) ? 1 : 0;
-    const K *gk = a.keys[src] + l.off;
-    const V *gv = a.vals[src] + l.off;
-    K *ok = a.keys[0] + l.off;
-    V *ov = a.vals[0] + l.off;
+    const typename Tr::K *gk = a.keys[src] + l.off;
+    const typename Tr::V *gv = a.vals[src] + l.off;
     const int len = l.len;
     // Coalesced load into shared memory, tail padded with the largest key.
-    for (int i = threadIdx.x; i < P; i += kThreads) {
-        sm.keys[pad32(i)] = i < len ? Ops::to_s(gk[i]) : Ops::s_largest();
-        if constexpr (Tr::KV) sm.vals[pad32(i)] = i < len ? gv[i] : 0;
-    }
+    for (int i = threadIdx.x; i < P; i += kThreads) sm.keys[pad32(i)] = i < len ? LK::load(gk, gv, i) : LK::largest();
     __syncthreads();
     S k[E];
-    V v[E];
-    smem_to_regs<kThreads, E, S, V, Tr::KV>(k, v, sm.keys, sm.vals);
+    smem_to_regs<E, S>(k, sm.keys);
     __syncthreads();
-    cta_bitonic_sort<kThreads, E, S, V, Tr::KV>(k, v, sm.keys, sm.vals);
-    regs_to_smem<kThreads, E, S, V, Tr::KV>(k, v, sm.keys, sm.vals);
+    cta_bitonic_sort<kThreads, E, S>(k, sm.keys);
+    regs_to_smem<E, S>(k, sm.keys);
     __syncthreads();
-    for (int i = threadIdx.x; i < len; i += kThreads) {
-        ok[i] = Ops::from_s(sm.keys[pad32(i)]);
-        if constexpr (Tr::KV) ov[i] = sm.vals[pad32(i)];
-    }
+    typename Tr::K *ok = a.keys[0] + l.off;
+    typename Tr::V *ov = a.vals[0] + l.off;
+    for (int i = threadIdx.x; i < len; i += kThreads) LK::store(ok, ov, i, sm.keys[pad32(i)]);
     __syncthreads();
 }
 
 template <class Tr, int E>
 __device__ void warp_leaf(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l)
 {
-    using K = typename Tr::K;
-    using V = typename Tr::V;
-    using Ops = KeyOps<K>;
-    using S = typename Ops::S;
+    using LK = LeafKey<Tr>;
+    using S = typename LK::S;
     const int lane = threadIdx.x & 31;
     const int src = (l.flags & kLeafScratch) ? 1 : 0;
-    const K *gk = a.keys[src] + l.off;
-    const V *gv = a.vals[src] + l.off;
-    K *ok = a.keys[0] + l.off;
-    V *ov = a.vals[0] + l.off;
+    const typename Tr::K *gk = a.keys[src] + l.off;
+    const typename Tr::V *gv = a.vals[src] + l.off;
     const int len = l.len;
     S k[E];
-    V v[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int i = lane * E + r;
-        k[r] = i < len ? Ops::to_s(gk[i]) : Ops::s_largest();
-        v[r] = 0;
-        if constexpr (Tr::KV) v[r] = i < len ? gv[i] : 0;
+        k[r] = i < len ? LK::load(gk, gv, i) : LK::largest();
     }
-    warp_bitonic_sort<E, S, V, Tr::KV>(k, v);
+    warp_bitonic_sort<E, S>(k);
+    typename Tr::K *ok = a.keys[0] + l.off;
+    typename Tr::V *ov = a.vals[0] + l.off;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int i = lane * E + r;
-        if (i < len) {
-            ok[i] = Ops::from_s(k[r]);
-            if constexpr (Tr::KV) ov[i] = v[r];
-        }
+        if (i < len) LK::store(ok, ov, i, k[r]);
     }
 }
 
