@@ -95,6 +95,31 @@ int qs_sort_host_f64(double *h_keys, int64_t n, qs_stream_t stream);
 int qs_sort_host_kv(int32_t *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream);
 
 /*
+ * qs_partition_i32 for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a service of the library, not part of
+ * the method.  The regular entry points grow a per-device workspace with
+ * cudaMalloc (and free it with cudaFree, which synchronises the device); a
+ * caller working inside a fixed device-memory budget owned by its own
+ * allocator, or one that must never cause that implicit synchronisation,
+ * cannot let them.  This variant allocates nothing: its scratch is one fixed
+ * file-scope device array of about 4.2 MiB that every GPU loading the library
+ * holds until the process exits.
+ *   - Same operation, arguments, result order and return value as
+ *     qs_partition_i32, for 0 <= n <= QS_NOALLOC_MAX_N; a larger n returns
+ *     QS_ERR_INVALID_ARG.  Errors come back as a negative qs_status only
+ *     (qs_last_error is not updated).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and the grid size; make that first call before
+ *     any stream capture.
+ *   - All calls share the one array: the library serialises calls made from
+ *     host threads, but work that overlaps on the GPU through any other route
+ *     would race on it.  The look-back words are cleared at the start of
+ *     every call; the rest is overwritten before it is read.
+ */
+#define QS_NOALLOC_MAX_N (1 << 20)
+int64_t qs_partition_i32_noalloc(int32_t *d_keys, int64_t n, int32_t pivot, qs_stream_t stream);
+
+/*
  * Grows the current device's workspace so that calls of `kind` with up to n
  * elements allocate nothing.  Returns QS_OK or a negative qs_status.
  */

@@ -72,6 +72,7 @@ def load() -> ctypes.CDLL:
             "qs_partition_i32": ([vp, i64, i32, vp], i64),
             "qs_partition_f64": ([vp, i64, f64, vp], i64),
             "qs_partition_kv": ([vp, vp, i64, i32, vp], i64),
+            "qs_partition_i32_noalloc": ([vp, i64, i32, vp], i64),
             "qs_sort_i32": ([vp, i64, vp], ci),
             "qs_sort_f64": ([vp, i64, vp], ci),
             "qs_sort_kv": ([vp, vp, i64, vp], ci),
