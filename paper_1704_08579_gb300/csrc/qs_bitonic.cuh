@@ -191,3 +191,120 @@ __device__ __forceinline__ void cta_bitonic_sort(S (&k)[E], S *sk)
 }
 
 }  // namespace qs
+
+namespace qs {
+
+// ---------------------------------------------------------------------------
+// Register-blocked Bitonic sort with layout transposes.
+//
+// A group of NG threads (a power of two, >= 32) holds P = NG*E elements, E =
+// 2^LE per thread.  A "layout c" keeps the element index bits [c, c+LE) in the
+// register index and the other bits, in order, in the thread index:
+//   index(g, r) = (g mod 2^c) | r << c | (g >> c) << (c + LE).
+// Every compare-exchange then runs between two registers of one thread; to
+// reach a stage on index bit d the group moves to a layout containing d by a
+// transpose through shared memory (one store and one load per element).
+// This is the direction-alternating form of Batcher's network (merge block
+// 2^m, stages on bits m-1 .. 0, descending where index bit m is set), which
+// needs single-bit stages only.  Padding with the largest key still ends up
+// at the tail: it is the largest value, and pads that tie with real keys are
+// bit-identical words.
+// ---------------------------------------------------------------------------
+template <int LE>
+__device__ __forceinline__ int lay_index(int g, int r, int c)
+{
+    return (g & ((1 << c) - 1)) | (r << c) | ((g >> c) << (c + LE));
+}
+
+template <int E, int LE, class S>
+__device__ __forceinline__ void lay_store(const S (&k)[E], S *sm, int g, int c)
+{
+#pragma unroll
+    for (int r = 0; r < E; ++r) sm[pad32(lay_index<LE>(g, r, c))] = k[r];
+}
+
+template <int E, int LE, class S>
+__device__ __forceinline__ void lay_load(S (&k)[E], const S *sm, int g, int c)
+{
+#pragma unroll
+    for (int r = 0; r < E; ++r) k[r] = sm[pad32(lay_index<LE>(g, r, c))];
+}
+
+__device__ __forceinline__ void group_sync(int bar, int nthreads)
+{
+    if (nthreads == 32)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
+}
+
+// One stage on register bit RB.  The sort direction of a pair comes from
+// register bit mrb of the register index (mrb >= 0) or is the same for the
+// whole thread (tdesc).
+template <int E, int RB, class S>
+__device__ __forceinline__ void reg_stage_b(S (&k)[E], int mrb, bool tdesc)
+{
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        if (r & (1 << RB)) continue;
+        const bool desc = mrb >= 0 ? ((r >> mrb) & 1) != 0 : tdesc;
+        S &a = k[r];
+        S &b = k[r | (1 << RB)];
+        const bool sw = (b < a) != desc;
+        const S lo = sw ? b : a;
+        b = sw ? a : b;
+        a = lo;
+    }
+}
+
+template <int E, int LE, class S>
+__device__ __forceinline__ void reg_stage(S (&k)[E], int rb, int mrb, bool tdesc)
+{
+    static_assert(LE >= 1 && LE <= 5, "2..32 registers per thread");
+    switch (rb) {
+    case 0: reg_stage_b<E, 0, S>(k, mrb, tdesc); break;
+    case 1: if constexpr (LE > 1) reg_stage_b<E, 1, S>(k, mrb, tdesc); break;
+    case 2: if constexpr (LE > 2) reg_stage_b<E, 2, S>(k, mrb, tdesc); break;
+    case 3: if constexpr (LE > 3) reg_stage_b<E, 3, S>(k, mrb, tdesc); break;
+    default: if constexpr (LE > 4) reg_stage_b<E, 4, S>(k, mrb, tdesc); break;
+    }
+}
+
+// Sorts the P = NG*E elements of a group.  On entry and exit the group holds
+// them in layout 0 (blocked: index = g*E + r); sm has room for pad32(P)
+// elements; g = thread index inside the group; L = log2(P).
+template <int E, int LE, class S>
+__device__ void group_bitonic_sort(S (&k)[E], S *sm, int g, int L, int bar, int nthreads)
+{
+    int cur = 0;
+    for (int m = 1; m <= L; ++m) {
+        for (int d = m - 1; d >= 0; --d) {
+            int c = (d / LE) * LE;
+            if (c > L - LE) c = L - LE;
+            if (c != cur) {
+                group_sync(bar, nthreads);
+                lay_store<E, LE, S>(k, sm, g, cur);
+                group_sync(bar, nthreads);
+                lay_load<E, LE, S>(k, sm, g, c);
+                cur = c;
+            }
+            int mrb = -1;
+            bool tdesc = false;  // the last merge (m == L) is ascending everywhere
+            if (m < L) {
+                if (m >= c && m < c + LE)
+                    mrb = m - c;
+                else
+                    tdesc = ((m < c ? (g >> m) : (g >> (m - LE))) & 1) != 0;
+            }
+            reg_stage<E, LE, S>(k, d - c, mrb, tdesc);
+        }
+    }
+    if (cur != 0) {
+        group_sync(bar, nthreads);
+        lay_store<E, LE, S>(k, sm, g, cur);
+        group_sync(bar, nthreads);
+        lay_load<E, LE, S>(k, sm, g, 0);
+    }
+}
+
+}  // namespace qs

@@ -48,10 +48,29 @@ struct LeafKey {
     }
 };
 
+// Registers per thread of the group network: 16 for 64-bit sort keys, 32 for
+// 32-bit ones, so a CTA of kThreads threads holds Tr::LEAF keys.
+template <class Tr>
+struct LeafCfg {
+    using S = typename LeafKey<Tr>::S;
+    static constexpr int E = sizeof(S) == 8 ? 16 : 32;
+    static constexpr int LE = sizeof(S) == 8 ? 4 : 5;
+    static_assert(kThreads * E == Tr::LEAF, "a CTA holds exactly one largest leaf");
+};
+
+struct LeafGroup {
+    Leaf leaf;
+    int start;     // first thread of the group
+    int nthreads;  // 32 .. kThreads
+};
+
 template <class Tr>
 struct LeafSmem {
     typename LeafKey<Tr>::S keys[Tr::LEAF + Tr::LEAF / 32];
-    Leaf leaf;
+    LeafGroup grp[kThreads / 32];
+    Leaf carry;
+    int has_carry;
+    int ngroups;
     long long idx;
 };
 
@@ -65,29 +84,35 @@ __device__ bool leaf_ok(const Args<typename Tr::K, typename Tr::V> &a, const Lea
     return ok;
 }
 
-template <class Tr, int E>
-__device__ void cta_leaf(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l, LeafSmem<Tr> &sm)
+// Sorts one leaf with a group of `nthreads` threads starting at thread
+// `start`; the group owns the shared-memory slice of its threads.
+template <class Tr>
+__device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l, LeafSmem<Tr> &sm, int start,
+                           int nthreads, int bar)
 {
     using LK = LeafKey<Tr>;
     using S = typename LK::S;
-    constexpr int P = kThreads * E;
+    constexpr int E = LeafCfg<Tr>::E, LE = LeafCfg<Tr>::LE;
+    S *gs = sm.keys + pad32(start * E);
+    const int g = threadIdx.x - start;
+    const int P = nthreads * E;
+    const int L = __ffs(P) - 1;
     const int src = (l.flags & kLeafScratch) ? 1 : 0;
     const typename Tr::K *gk = a.keys[src] + l.off;
     const typename Tr::V *gv = a.vals[src] + l.off;
     const int len = l.len;
-    // Coalesced load into shared memory, tail padded with the largest key.
-    for (int i = threadIdx.x; i < P; i += kThreads) sm.keys[pad32(i)] = i < len ? LK::load(gk, gv, i) : LK::largest();
-    __syncthreads();
+    // Coalesced load, tail padded with the largest key.
+    for (int i = g; i < P; i += nthreads) gs[pad32(i)] = i < len ? LK::load(gk, gv, i) : LK::largest();
+    group_sync(bar, nthreads);
     S k[E];
-    smem_to_regs<E, S>(k, sm.keys);
-    __syncthreads();
-    cta_bitonic_sort<kThreads, E, S>(k, sm.keys);
-    regs_to_smem<E, S>(k, sm.keys);
-    __syncthreads();
+    lay_load<E, LE, S>(k, gs, g, 0);
+    group_bitonic_sort<E, LE, S>(k, gs, g, L, bar, nthreads);
+    group_sync(bar, nthreads);
+    lay_store<E, LE, S>(k, gs, g, 0);
+    group_sync(bar, nthreads);
     typename Tr::K *ok = a.keys[0] + l.off;
     typename Tr::V *ov = a.vals[0] + l.off;
-    for (int i = threadIdx.x; i < len; i += kThreads) LK::store(ok, ov, i, sm.keys[pad32(i)]);
-    __syncthreads();
+    for (int i = g; i < len; i += nthreads) LK::store(ok, ov, i, gs[pad32(i)]);
 }
 
 template <class Tr, int E>
@@ -130,37 +155,64 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
     __syncthreads();
     const long long n_large = static_cast<long long>(ld_relaxed_u64(&c->n_large));
     const long long n_small = static_cast<long long>(ld_relaxed_u64(&c->n_small));
-    constexpr int kE16 = Tr::LEAF >= kThreads * 16 ? 16 : Tr::LEAF / kThreads;
-    constexpr int kE32 = Tr::LEAF >= kThreads * 32 ? 32 : kE16;
+    constexpr int E = LeafCfg<Tr>::E;
+    if (tid == 0) sm.has_carry = 0;
+    // Large parts: thread 0 packs parts into thread groups (32 .. kThreads
+    // threads each, E keys per thread); a part that does not fit is carried
+    // over to this CTA's next round.
     for (;;) {
         if (tid == 0) {
-            sm.idx = static_cast<long long>(atomicAdd(&c->claim_large, 1ull));
-            if (sm.idx < n_large) {
-                sm.leaf = a.leaves[sm.idx];
-                if (!leaf_ok<Tr>(a, sm.leaf, false)) sm.leaf.len = 0;
+            int ng = 0, used = 0;
+            for (;;) {
+                Leaf l;
+                if (sm.has_carry) {
+                    l = sm.carry;
+                    sm.has_carry = 0;
+                } else {
+                    const long long idx = static_cast<long long>(atomicAdd(&c->claim_large, 1ull));
+                    if (idx >= n_large) break;
+                    l = a.leaves[idx];
+                    if (!leaf_ok<Tr>(a, l, false)) continue;
+                }
+                int need = kThreads;
+                if (!(l.flags & kLeafFinal)) {
+                    need = 32;
+                    while (need * E < l.len) need *= 2;
+                }
+                if (used + need > kThreads) {
+                    sm.carry = l;
+                    sm.has_carry = 1;
+                    break;
+                }
+                sm.grp[ng].leaf = l;
+                sm.grp[ng].start = used;
+                sm.grp[ng].nthreads = need;
+                ++ng;
+                used += need;
+                if (used == kThreads) break;
+            }
+            sm.ngroups = ng;
+        }
+        __syncthreads();
+        const int ng = sm.ngroups;
+        if (ng == 0) break;
+        int gi = -1;
+        for (int i = 0; i < ng; ++i)
+            if (tid >= sm.grp[i].start && tid < sm.grp[i].start + sm.grp[i].nthreads) gi = i;
+        if (gi >= 0) {
+            const Leaf l = sm.grp[gi].leaf;
+            if (l.flags & kLeafFinal) {
+                const K *gk = a.keys[1] + l.off;
+                const V *gv = a.vals[1] + l.off;
+                for (int i = tid; i < l.len; i += kThreads) {
+                    a.keys[0][l.off + i] = gk[i];
+                    if constexpr (Tr::KV) a.vals[0][l.off + i] = gv[i];
+                }
+            } else {
+                group_leaf<Tr>(a, l, sm, sm.grp[gi].start, sm.grp[gi].nthreads, gi + 1);
             }
         }
         __syncthreads();
-        const long long idx = sm.idx;
-        const Leaf l = sm.leaf;
-        __syncthreads();
-        if (idx >= n_large) break;
-        if (l.len == 0) continue;
-        if (l.flags & kLeafFinal) {
-            const K *gk = a.keys[1] + l.off;
-            const V *gv = a.vals[1] + l.off;
-            for (int i = tid; i < l.len; i += kThreads) {
-                a.keys[0][l.off + i] = gk[i];
-                if constexpr (Tr::KV) a.vals[0][l.off + i] = gv[i];
-            }
-            continue;
-        }
-        const int len = l.len;
-        if (len <= kThreads * 2) cta_leaf<Tr, 2>(a, l, sm);
-        else if (len <= kThreads * 4) cta_leaf<Tr, 4>(a, l, sm);
-        else if (len <= kThreads * 8) cta_leaf<Tr, 8>(a, l, sm);
-        else if (len <= kThreads * 16 || kE32 == kE16) cta_leaf<Tr, kE16>(a, l, sm);
-        else cta_leaf<Tr, kE32>(a, l, sm);
     }
     // Small parts: one warp each.
     for (;;) {
