@@ -210,24 +210,45 @@ namespace qs {
 // at the tail: it is the largest value, and pads that tie with real keys are
 // bit-identical words.
 // ---------------------------------------------------------------------------
-template <int LE>
-__device__ __forceinline__ int lay_index(int g, int r, int c)
+// Shared-memory slot of element i: one pad word per 128 bytes keeps every
+// layout's accesses free of bank conflicts (PSH = 4 for 8-byte keys, 5 for
+// 4-byte keys).
+template <class S>
+__device__ __forceinline__ int padk(int i)
 {
-    return (g & ((1 << c) - 1)) | (r << c) | ((g >> c) << (c + LE));
+    constexpr int PSH = sizeof(S) == 8 ? 4 : 5;
+    return i + (i >> PSH);
+}
+
+// In layout c the E slots of a thread are base + r*stride (all layouts used
+// have c == 0 or c >= PSH, where the padding is linear in r).
+template <int LE, class S>
+__device__ __forceinline__ void lay_addr(int g, int c, int &base, int &stride)
+{
+    constexpr int PSH = sizeof(S) == 8 ? 4 : 5;
+    const int low = g & ((1 << c) - 1), high = g >> c;
+    base = padk<S>(low | (high << (c + LE)));
+    stride = c == 0 ? 1 : (1 << c) + (1 << (c - PSH));
 }
 
 template <int E, int LE, class S>
 __device__ __forceinline__ void lay_store(const S (&k)[E], S *sm, int g, int c)
 {
+    int base, stride;
+    lay_addr<LE, S>(g, c, base, stride);
+    S *p = sm + base;
 #pragma unroll
-    for (int r = 0; r < E; ++r) sm[pad32(lay_index<LE>(g, r, c))] = k[r];
+    for (int r = 0; r < E; ++r) p[r * stride] = k[r];
 }
 
 template <int E, int LE, class S>
 __device__ __forceinline__ void lay_load(S (&k)[E], const S *sm, int g, int c)
 {
+    int base, stride;
+    lay_addr<LE, S>(g, c, base, stride);
+    const S *p = sm + base;
 #pragma unroll
-    for (int r = 0; r < E; ++r) k[r] = sm[pad32(lay_index<LE>(g, r, c))];
+    for (int r = 0; r < E; ++r) k[r] = p[r * stride];
 }
 
 __device__ __forceinline__ void group_sync(int bar, int nthreads)
@@ -238,35 +259,75 @@ __device__ __forceinline__ void group_sync(int bar, int nthreads)
         asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
 }
 
-// One stage on register bit RB.  The sort direction of a pair comes from
-// register bit mrb of the register index (mrb >= 0) or is the same for the
-// whole thread (tdesc).
-template <int E, int RB, class S>
-__device__ __forceinline__ void reg_stage_b(S (&k)[E], int mrb, bool tdesc)
+// Ordered pair: (min, max) ascending, (max, min) descending.
+template <bool DESC, class S>
+__device__ __forceinline__ void cx_dir(S &a, S &b)
+{
+    if constexpr (sizeof(S) == 4) {
+        const S lo = min(a, b), hi = max(a, b);
+        a = DESC ? hi : lo;
+        b = DESC ? lo : hi;
+    } else {
+        const bool sw = DESC ? (a < b) : (b < a);
+        const S x = sw ? b : a;
+        b = sw ? a : b;
+        a = x;
+    }
+}
+
+// One stage on register bit RB with the same direction for the whole thread.
+template <int E, int RB, bool DESC, class S>
+__device__ __forceinline__ void reg_stage_u(S (&k)[E])
+{
+#pragma unroll
+    for (int r = 0; r < E; ++r)
+        if (!(r & (1 << RB))) cx_dir<DESC, S>(k[r], k[r | (1 << RB)]);
+}
+
+// One stage on register bit RB whose direction is register bit MRB.
+template <int E, int RB, int MRB, class S>
+__device__ __forceinline__ void reg_stage_p(S (&k)[E])
 {
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         if (r & (1 << RB)) continue;
-        const bool desc = mrb >= 0 ? ((r >> mrb) & 1) != 0 : tdesc;
-        S &a = k[r];
-        S &b = k[r | (1 << RB)];
-        const bool sw = (b < a) != desc;
-        const S lo = sw ? b : a;
-        b = sw ? a : b;
-        a = lo;
+        if ((r >> MRB) & 1)
+            cx_dir<true, S>(k[r], k[r | (1 << RB)]);
+        else
+            cx_dir<false, S>(k[r], k[r | (1 << RB)]);
     }
 }
 
+template <int E, int RB, class S>
+__device__ __forceinline__ void reg_stage_rb(S (&k)[E], int mrb, bool tdesc)
+{
+    switch (mrb) {
+    case -1:
+        if (tdesc)
+            reg_stage_u<E, RB, true, S>(k);
+        else
+            reg_stage_u<E, RB, false, S>(k);
+        break;
+    case 1: if constexpr (RB < 1 && E > 2) reg_stage_p<E, RB, 1, S>(k); break;
+    case 2: if constexpr (RB < 2 && E > 4) reg_stage_p<E, RB, 2, S>(k); break;
+    case 3: if constexpr (RB < 3 && E > 8) reg_stage_p<E, RB, 3, S>(k); break;
+    case 4: if constexpr (RB < 4 && E > 16) reg_stage_p<E, RB, 4, S>(k); break;
+    default: break;
+    }
+}
+
+// A stage on register bit rb; mrb = register bit holding the direction, or -1
+// when the direction is the same for the whole thread (tdesc).
 template <int E, int LE, class S>
 __device__ __forceinline__ void reg_stage(S (&k)[E], int rb, int mrb, bool tdesc)
 {
     static_assert(LE >= 1 && LE <= 5, "2..32 registers per thread");
     switch (rb) {
-    case 0: reg_stage_b<E, 0, S>(k, mrb, tdesc); break;
-    case 1: if constexpr (LE > 1) reg_stage_b<E, 1, S>(k, mrb, tdesc); break;
-    case 2: if constexpr (LE > 2) reg_stage_b<E, 2, S>(k, mrb, tdesc); break;
-    case 3: if constexpr (LE > 3) reg_stage_b<E, 3, S>(k, mrb, tdesc); break;
-    default: if constexpr (LE > 4) reg_stage_b<E, 4, S>(k, mrb, tdesc); break;
+    case 0: reg_stage_rb<E, 0, S>(k, mrb, tdesc); break;
+    case 1: if constexpr (LE > 1) reg_stage_rb<E, 1, S>(k, mrb, tdesc); break;
+    case 2: if constexpr (LE > 2) reg_stage_rb<E, 2, S>(k, mrb, tdesc); break;
+    case 3: if constexpr (LE > 3) reg_stage_rb<E, 3, S>(k, mrb, tdesc); break;
+    default: if constexpr (LE > 4) reg_stage_rb<E, 4, S>(k, mrb, tdesc); break;
     }
 }
 

@@ -66,7 +66,7 @@ struct LeafGroup {
 
 template <class Tr>
 struct LeafSmem {
-    typename LeafKey<Tr>::S keys[Tr::LEAF + Tr::LEAF / 32];
+    typename LeafKey<Tr>::S keys[Tr::LEAF + Tr::LEAF / 16];
     LeafGroup grp[kThreads / 32];
     Leaf carry;
     int has_carry;
@@ -93,7 +93,7 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     using LK = LeafKey<Tr>;
     using S = typename LK::S;
     constexpr int E = LeafCfg<Tr>::E, LE = LeafCfg<Tr>::LE;
-    S *gs = sm.keys + pad32(start * E);
+    S *gs = sm.keys + padk<S>(start * E);
     const int g = threadIdx.x - start;
     const int P = nthreads * E;
     const int L = __ffs(P) - 1;
@@ -102,7 +102,7 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     const typename Tr::V *gv = a.vals[src] + l.off;
     const int len = l.len;
     // Coalesced load, tail padded with the largest key.
-    for (int i = g; i < P; i += nthreads) gs[pad32(i)] = i < len ? LK::load(gk, gv, i) : LK::largest();
+    for (int i = g; i < P; i += nthreads) gs[padk<S>(i)] = i < len ? LK::load(gk, gv, i) : LK::largest();
     group_sync(bar, nthreads);
     S k[E];
     lay_load<E, LE, S>(k, gs, g, 0);
@@ -112,7 +112,7 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     group_sync(bar, nthreads);
     typename Tr::K *ok = a.keys[0] + l.off;
     typename Tr::V *ov = a.vals[0] + l.off;
-    for (int i = g; i < len; i += nthreads) LK::store(ok, ov, i, gs[pad32(i)]);
+    for (int i = g; i < len; i += nthreads) LK::store(ok, ov, i, gs[padk<S>(i)]);
 }
 
 template <class Tr, int E>
