@@ -323,6 +323,7 @@ def run_ours(args):
         line["e2e"] = _e2e(torch, qs, host, stream, args)
         if not args.no_extra:
             line["extra"] = _extras(torch, qs, stream, hbm_peak)
+            line["batched"] = _batched(torch, qs, stream)
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_oracle_baseline()
         print(json.dumps(line), flush=True)
@@ -346,6 +347,60 @@ def _e2e(torch, qs, host, stream, args):
     del pinned, arrs
     return {"value": N_KEYS / dt / 1e9, "unit": "Gkeys/s", "h2d_bytes_per_step": N_KEYS * 8,
             "d2h_bytes_per_step": N_KEYS * 8, "ms_per_step": dt * 1e3, "steps": steps, "sorted": ok}
+
+
+def _batched(torch, qs, stream, nseg=20_000, steps=3):
+    """Batched segmented sort (20,000 int32 arrays, log-uniform sizes in [16, 2^18])
+    in one graph-captured launch sequence with autotuned leaf/one-warp thresholds,
+    against the plain form: one qs_sort_i32 call per array."""
+    from paper_1704_08579_gb300 import autotune
+
+    out = {}
+    for kind in ("i32", "kv"):
+        keys, offs = synth.segments_i32(nseg)
+        n = keys.size
+        dk = torch.from_numpy(keys).to("cuda")
+        dv = torch.arange(n, dtype=torch.int32, device="cuda") if kind == "kv" else None
+        doffs = torch.from_numpy(offs).to("cuda")
+        tuned = autotune.tune(dk, doffs, dv, reps=1, use_cache=False, stream=stream)
+        bk = [dk.clone() for _ in range(steps)]
+        bv = [dv.clone() for _ in range(steps)] if dv is not None else None
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            for i in range(steps):
+                qs.sort_segmented(bk[i], doffs, None if bv is None else bv[i], stream=stream)
+            b.record(stream)
+        b.synchronize()
+        ms_batched = a.elapsed_time(b) / steps
+        ok = bool(((bk[0][1:] >= bk[0][:-1]) | (torch.isin(torch.arange(1, n, device="cuda"), doffs))).all())
+        del bk, bv
+        autotune.apply({})  # back to the compiled defaults for the plain form
+        # Plain form: one sort call (one launch sequence) per array.
+        pk = dk.clone()
+        pv = dv.clone() if dv is not None else None
+        bounds = offs.tolist()
+        torch.cuda.synchronize()
+        a2 = torch.cuda.Event(enable_timing=True)
+        b2 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a2.record(stream)
+            for i in range(nseg):
+                lo, hi = bounds[i], bounds[i + 1]
+                if hi - lo > 1:
+                    qs.sort(pk[lo:hi], None if pv is None else pv[lo:hi], stream=stream)
+            b2.record(stream)
+        b2.synchronize()
+        ms_plain = a2.elapsed_time(b2)
+        out[kind] = {"workload": "%d %s arrays, sizes log-uniform [16, 2^18], %d keys" % (nseg, kind, n),
+                     "batched_ms": ms_batched, "batched_gkeys_s": n / (ms_batched / 1e3) / 1e9,
+                     "plain_per_array_ms": ms_plain, "plain_gkeys_s": n / (ms_plain / 1e3) / 1e9,
+                     "speedup": ms_plain / ms_batched, "tuned": {k: tuned[k] for k in ("leaf_max", "small_max")},
+                     "batched_sorted": ok}
+        del dk, dv, pk, pv
+        torch.cuda.empty_cache()
+    return out
 
 
 def _extras(torch, qs, stream, hbm_peak):

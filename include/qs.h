@@ -85,6 +85,23 @@ int qs_sort_f64(double *d_keys, int64_t n, qs_stream_t stream);
 int qs_sort_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, qs_stream_t stream);
 
 /*
+ * Batched (segmented) sort: sorts every segment [d_offsets[i], d_offsets[i+1])
+ * of d_keys (and d_vals) in place, i = 0 .. nseg-1, independently.  d_offsets
+ * is a DEVICE array of nseg+1 int64 offsets with 0 <= d_offsets[i] <=
+ * d_offsets[i+1] <= n (checked on the device: a bad table returns
+ * QS_ERR_INVALID_ARG and leaves the keys unspecified).  All segments are sorted
+ * by one setup pass, one launch of the persistent partition kernel and one
+ * launch of the leaf kernel; these are captured once per argument set into a
+ * CUDA graph and replayed.  Same method and return convention as qs_sort_*.
+ */
+int qs_sort_segmented_i32(int32_t *d_keys, int64_t n, const int64_t *d_offsets, int64_t nseg,
+                          qs_stream_t stream);
+int qs_sort_segmented_f64(double *d_keys, int64_t n, const int64_t *d_offsets, int64_t nseg,
+                          qs_stream_t stream);
+int qs_sort_segmented_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, const int64_t *d_offsets,
+                         int64_t nseg, qs_stream_t stream);
+
+/*
  * Host-buffer sorts: h_keys (and h_vals) are HOST pointers (pinned memory is
  * fastest).  The library copies them into a device staging area owned by the
  * workspace, sorts there with the qs_sort_* path, and copies the result back,
@@ -177,12 +194,22 @@ int qs_get_stats(qs_stats *out);
  *                        QS_ERR_CAPACITY); 0 = size from n.
  *   QS_OPT_DRIVER_CTAS   if > 0, number of CTAs of the persistent kernels;
  *                        0 = all resident CTAs.
+ *   QS_OPT_LEAF_MAX      parts of at most this many keys (a power of two,
+ *                        >= 32) go to the Bitonic leaf kernel; 0 = the
+ *                        compiled maximum (4096 f64/kv, 8192 i32), larger
+ *                        values are clamped to it.
+ *   QS_OPT_SMALL_MAX     parts of at most this many keys (power of two, >= 32)
+ *                        are sorted by one warp; 0 = the compiled maximum 512.
+ * The tuning options are what the autotuner (paper_1704_08579_gb300.autotune)
+ * searches.
  */
 enum {
     QS_OPT_PROFILE = 1,
     QS_OPT_WAIT_LIMIT_NS = 2,
     QS_OPT_TASK_CAP = 3,
-    QS_OPT_DRIVER_CTAS = 4
+    QS_OPT_DRIVER_CTAS = 4,
+    QS_OPT_LEAF_MAX = 5,
+    QS_OPT_SMALL_MAX = 6
 };
 int qs_set_option(int option, int64_t value);
 

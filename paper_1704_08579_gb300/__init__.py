@@ -30,7 +30,7 @@ STATUS = {
     -5: "QS_ERR_TIMEOUT", -6: "QS_ERR_CAPACITY", -7: "QS_ERR_INTERNAL",
 }
 KIND = {"i32": 0, "f64": 1, "kv": 2}
-OPTION = {"profile": 1, "wait_limit_ns": 2, "task_cap": 3, "driver_ctas": 4}
+OPTION = {"profile": 1, "wait_limit_ns": 2, "task_cap": 3, "driver_ctas": 4, "leaf_max": 5, "small_max": 6}
 
 _lib = None
 _lock = threading.Lock()
@@ -76,6 +76,9 @@ def load() -> ctypes.CDLL:
             "qs_sort_i32": ([vp, i64, vp], ci),
             "qs_sort_f64": ([vp, i64, vp], ci),
             "qs_sort_kv": ([vp, vp, i64, vp], ci),
+            "qs_sort_segmented_i32": ([vp, i64, vp, i64, vp], ci),
+            "qs_sort_segmented_f64": ([vp, i64, vp, i64, vp], ci),
+            "qs_sort_segmented_kv": ([vp, vp, i64, vp, i64, vp], ci),
             "qs_sort_host_i32": ([vp, i64, vp], ci),
             "qs_sort_host_f64": ([vp, i64, vp], ci),
             "qs_sort_host_kv": ([vp, vp, i64, vp], ci),
@@ -166,6 +169,32 @@ def sort(keys, values=None, stream=None) -> None:
         _check(lib.qs_sort_i32(keys.data_ptr(), n, s))
     else:
         _check(lib.qs_sort_f64(keys.data_ptr(), n, s))
+
+
+def sort_segmented(keys, offsets, values=None, stream=None) -> None:
+    """qs_sort_segmented_*: sorts every segment [offsets[i], offsets[i+1]) of keys in place.
+
+    ``offsets`` is a CUDA int64 tensor of nseg + 1 entries."""
+    import torch
+
+    lib = load()
+    kind = _kind_of(keys, values)
+    _check_tensor(keys, "keys")
+    _check_tensor(offsets, "offsets")
+    if offsets.dtype != torch.int64:
+        raise TypeError("offsets must be int64")
+    s = _stream_handle(stream)
+    n = keys.numel()
+    nseg = max(offsets.numel() - 1, 0)
+    if kind == "kv":
+        _check_tensor(values, "values")
+        if values.numel() != n:
+            raise ValueError("keys and values differ in length")
+        _check(lib.qs_sort_segmented_kv(keys.data_ptr(), values.data_ptr(), n, offsets.data_ptr(), nseg, s))
+    elif kind == "i32":
+        _check(lib.qs_sort_segmented_i32(keys.data_ptr(), n, offsets.data_ptr(), nseg, s))
+    else:
+        _check(lib.qs_sort_segmented_f64(keys.data_ptr(), n, offsets.data_ptr(), nseg, s))
 
 
 def sort_host(keys, values=None, stream=None) -> None:

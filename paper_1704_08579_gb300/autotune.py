@@ -1,0 +1,100 @@
+"""Autotuner for the run-time knobs of the sort: the leaf threshold (largest
+part handed to the Bitonic kernel, QS_OPT_LEAF_MAX) and the one-warp threshold
+(QS_OPT_SMALL_MAX).  Each candidate is timed on the caller's own data with
+CUDA events (a fresh copy of the input per run, so every run sorts the same
+unsorted data); the fastest is kept, applied with qs_set_option, and recorded
+in a JSON cache keyed by GPU name and workload signature.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+import paper_1704_08579_gb300 as qs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE_DIR = os.path.join(HERE, "tuning")
+
+LEAF_CHOICES = {"i32": (2048, 4096, 8192), "f64": (1024, 2048, 4096), "kv": (1024, 2048, 4096)}
+SMALL_CHOICES = (128, 256, 512)
+
+
+def _cache_path(gpu_name: str) -> str:
+    safe = "".join(ch if ch.isalnum() else "_" for ch in gpu_name)
+    return os.path.join(CACHE_DIR, safe + ".json")
+
+
+def _load_cache(gpu_name: str) -> dict:
+    p = _cache_path(gpu_name)
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def _store_cache(gpu_name: str, cache: dict) -> None:
+    os.makedirs(CACHE_DIR, exist_ok=True)
+    tmp = _cache_path(gpu_name) + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, _cache_path(gpu_name))
+
+
+def signature(kind: str, n: int, nseg: int) -> str:
+    """Workload key: kind, log2 of the key count, log2 of the segment count."""
+    return "%s:n2^%d:seg2^%d" % (kind, max(n, 1).bit_length() - 1, max(nseg, 1).bit_length() - 1)
+
+
+def apply(cfg: dict) -> None:
+    qs.set_option("leaf_max", int(cfg.get("leaf_max", 0)))
+    qs.set_option("small_max", int(cfg.get("small_max", 0)))
+
+
+def tune(keys, offsets=None, values=None, reps: int = 2, use_cache: bool = True, stream=None) -> dict:
+    """Tunes (leaf_max, small_max) for sorting `keys` (CUDA tensor), segmented by
+    `offsets` if given; returns {"leaf_max", "small_max", "ms", "table"} and
+    leaves the winner applied.  The input tensors are not modified."""
+    import torch
+
+    kind = "kv" if values is not None else ("i32" if keys.dtype == torch.int32 else "f64")
+    nseg = 1 if offsets is None else offsets.numel() - 1
+    gpu = torch.cuda.get_device_name()
+    sig = signature(kind, keys.numel(), nseg)
+    cache = _load_cache(gpu) if use_cache else {}
+    if use_cache and sig in cache:
+        apply(cache[sig])
+        return dict(cache[sig], cached=True)
+    stream = stream or torch.cuda.current_stream()
+    work_k = torch.empty_like(keys)
+    work_v = torch.empty_like(values) if values is not None else None
+    table = []
+    for leaf in LEAF_CHOICES[kind]:
+        for small in SMALL_CHOICES:
+            if small > leaf:
+                continue
+            apply({"leaf_max": leaf, "small_max": small})
+            times = []
+            for _ in range(reps + 1):  # the first run warms up (and captures the graph)
+                work_k.copy_(keys)
+                if work_v is not None:
+                    work_v.copy_(values)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    a.record(stream)
+                    if offsets is None:
+                        qs.sort(work_k, work_v, stream=stream)
+                    else:
+                        qs.sort_segmented(work_k, offsets, work_v, stream=stream)
+                    b.record(stream)
+                b.synchronize()
+                times.append(a.elapsed_time(b))
+            table.append({"leaf_max": leaf, "small_max": small, "ms": statistics.median(times[1:])})
+    best = min(table, key=lambda r: r["ms"])
+    result = {"leaf_max": best["leaf_max"], "small_max": best["small_max"], "ms": best["ms"], "table": table}
+    apply(result)
+    if use_cache:
+        cache[sig] = {k: result[k] for k in ("leaf_max", "small_max", "ms")}
+        _store_cache(gpu, cache)
+    return result

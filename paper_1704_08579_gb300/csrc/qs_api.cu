@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/qs.h"
 #include "qs_internal.h"
@@ -24,6 +25,8 @@ std::atomic<int> g_profile{0};
 std::atomic<int64_t> g_wait_limit_ns{2000000000ll};
 std::atomic<int64_t> g_task_cap{0};
 std::atomic<int64_t> g_driver_ctas{0};
+std::atomic<int64_t> g_leaf_max{0};   // 0 = the kind's compiled maximum
+std::atomic<int64_t> g_small_max{0};  // 0 = the kind's compiled maximum
 
 constexpr int64_t kMaxN = 1ll << 38;
 
@@ -64,7 +67,20 @@ struct Workspace {
     Ctrl *h_ctrl = nullptr;
     bool dirty = true;  // look-back words / ticket owners must be cleared before use
     cudaEvent_t ev[6] = {};
+    cudaStream_t capture = nullptr;  // private stream used to capture CUDA graphs
+    struct Graph {
+        std::string key;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<Graph> graphs;  // segmented sorts, most recent last
 };
+
+void drop_graphs(Workspace &w)
+{
+    for (auto &g : w.graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    w.graphs.clear();
+}
 
 constexpr int kMaxDevices = 64;
 Workspace *g_ws[kMaxDevices] = {};
@@ -140,24 +156,38 @@ struct Needs {
     int64_t task_cap, pool_cap, leaf_cap;
 };
 
-Needs needs_for(int64_t n, int kind)
+int64_t leaf_max_of(int kind)
+{
+    const int64_t compiled = limits_of(kind).leaf_max, want = g_leaf_max.load();
+    return want > 0 && want < compiled ? want : compiled;
+}
+
+int64_t small_max_of(int kind)
+{
+    const int64_t compiled = limits_of(kind).small_max, want = g_small_max.load();
+    const int64_t v = want > 0 && want < compiled ? want : compiled;
+    return v < leaf_max_of(kind) ? v : leaf_max_of(kind);
+}
+
+Needs needs_for(int64_t n, int kind, int64_t nseg = 0)
 {
     const KernelLimits l = limits_of(kind);
     Needs r;
     r.key_bytes = static_cast<size_t>(n) * (kind == QS_KIND_F64 ? 8 : 4);
     r.val_bytes = kind == QS_KIND_KV ? static_cast<size_t>(n) * 4 : 0;
     const int64_t cap_override = g_task_cap.load();
-    r.task_cap = cap_override > 0 ? cap_override : 8 * (n / l.leaf_max) + 1024;
+    r.task_cap = cap_override > 0 ? cap_override : 8 * (n / leaf_max_of(kind)) + 1024 + nseg;
     r.pool_cap = 64 * (n / l.tile + 1) + 2 * r.task_cap + 4096;
-    r.leaf_cap = 4 * r.task_cap + n / kCopyChunk + 1024;
+    r.leaf_cap = 4 * r.task_cap + n / kCopyChunk + 1024 + nseg;
     return r;
 }
 
-int ws_ensure(Workspace &w, int64_t n, int kind)
+int ws_ensure(Workspace &w, int64_t n, int kind, int64_t nseg = 0)
 {
     int rc = ws_init(w);
     if (rc) return rc;
-    const Needs nd = needs_for(n, kind);
+    const Needs nd = needs_for(n, kind, nseg);
+    const void *before[] = {w.scratch_k, w.scratch_v, w.tasks, w.pool, w.owner, w.leaves};
     if ((rc = grow(&w.scratch_k, &w.scratch_k_bytes, nd.key_bytes, "scratch keys"))) return rc;
     if (nd.val_bytes && (rc = grow(&w.scratch_v, &w.scratch_v_bytes, nd.val_bytes, "scratch values"))) return rc;
     const bool override_cap = g_task_cap.load() > 0;
@@ -187,6 +217,12 @@ int ws_ensure(Workspace &w, int64_t n, int kind)
         if ((rc = grow(reinterpret_cast<void **>(&w.leaves), &have, nd.leaf_cap * sizeof(Leaf), "leaf list"))) return rc;
         w.leaf_cap = nd.leaf_cap;
     }
+    const void *after[] = {w.scratch_k, w.scratch_v, w.tasks, w.pool, w.owner, w.leaves};
+    for (int i = 0; i < 6; ++i)
+        if (before[i] != after[i]) {
+            drop_graphs(w);  // captured graphs point at the old buffers
+            break;
+        }
     return QS_OK;
 }
 
@@ -194,6 +230,9 @@ void ws_free(Workspace &w)
 {
     if (!w.init) return;
     cudaDeviceSynchronize();
+    drop_graphs(w);
+    if (w.capture) cudaStreamDestroy(w.capture);
+    w.capture = nullptr;
     void *bufs[] = {w.scratch_k, w.scratch_v, w.stage_k, w.stage_v, w.tasks, w.owner, w.pool, w.leaves, w.ctrl};
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -234,13 +273,17 @@ const char *status_text(int s)
 // current device.  keys/vals are device pointers.
 template <class K>
 int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, int partition_only,
-            qs_stream_t stream)
+            qs_stream_t stream, const int64_t *seg_off = nullptr, int64_t nseg = 0)
 {
     t_error.clear();
     std::memset(&t_stats, 0, sizeof(t_stats));
     t_stats.n = n;
     t_stats.kind = kind;
     if (n < 0 || n > kMaxN) return fail(QS_ERR_INVALID_ARG, "n = %lld out of range [0, 2^38]", (long long)n);
+    if (nseg < 0 || nseg > (1ll << 31)) return fail(QS_ERR_INVALID_ARG, "nseg = %lld out of range", (long long)nseg);
+    if (nseg > 0 && !seg_off) return fail(QS_ERR_INVALID_ARG, "null offsets pointer");
+    if (seg_off && reinterpret_cast<uintptr_t>(seg_off) % 8) return fail(QS_ERR_ALIGN, "offsets not aligned to 8 bytes");
+    if (seg_off && nseg == 0) return QS_OK;
     if (n == 0 || (n == 1 && !partition_only)) {
         if (partition_only) return 0;
         return QS_OK;
@@ -255,7 +298,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     if (dev < 0 || dev >= kMaxDevices) return fail(QS_ERR_INVALID_ARG, "device %d out of range", dev);
     Workspace &w = *workspace_for(dev);
     std::lock_guard<std::mutex> guard(w.mu);
-    int rc = ws_ensure(w, n, kind);
+    int rc = ws_ensure(w, n, kind, nseg);
     if (rc) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (w.dirty) {
@@ -285,12 +328,15 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     a.task_cap = w.task_cap;
     a.pool_cap = w.pool_cap;
     a.leaf_cap = w.leaf_cap;
-    a.leaf_max = lim.leaf_max;
-    a.small_max = lim.small_max;
+    a.leaf_max = leaf_max_of(kind);
+    a.small_max = small_max_of(kind);
     a.wait_limit_ns = static_cast<uint64_t>(g_wait_limit_ns.load());
     a.pivot_bits = pivot_bits;
     a.partition_only = partition_only;
     a.profile = g_profile.load();
+    a.seg_off = seg_off;
+    a.nseg = nseg;
+    (void)lim;
 
     LaunchCfg cfg;
     std::memset(&cfg, 0, sizeof(cfg));
@@ -301,14 +347,51 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     cfg.profile = g_profile.load();
     for (int i = 0; i < 6; ++i) cfg.ev[i] = w.ev[i];
 
-    int le = 0;
-    if constexpr (sizeof(K) == 8)
-        le = launch_f64(a, cfg);
-    else
-        le = kind == QS_KIND_I32 ? launch_i32(a, cfg) : launch_kv(a, cfg);
-    if (le != cudaSuccess) return cuda_fail(static_cast<cudaError_t>(le), "kernel launch");
-    if ((e = cudaMemcpyAsync(w.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(e, "cudaMemcpyAsync(status)");
+    auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+        LaunchCfg c2 = cfg;
+        c2.stream = st;
+        int le = 0;
+        if constexpr (sizeof(K) == 8)
+            le = launch_f64(a, c2);
+        else
+            le = kind == QS_KIND_I32 ? launch_i32(a, c2) : launch_kv(a, c2);
+        if (le != cudaSuccess) return static_cast<cudaError_t>(le);
+        return cudaMemcpyAsync(w.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+    };
+    if (seg_off) {
+        // Segmented sorts replay one CUDA graph (setup, persistent partition
+        // kernel, leaf kernel, status read-back) per argument set.
+        cfg.profile = 0;
+        char key[320];
+        snprintf(key, sizeof(key), "%d:%p:%p:%p:%lld:%lld:%lld:%lld:%d:%d:%llu", kind, (void *)keys, (void *)vals,
+                 (const void *)seg_off, (long long)n, (long long)nseg, (long long)a.leaf_max, (long long)a.small_max,
+                 cfg.grid_driver, cfg.grid_leaf, (unsigned long long)a.wait_limit_ns);
+        cudaGraphExec_t exec = nullptr;
+        for (auto &g : w.graphs)
+            if (g.key == key) exec = g.exec;
+        if (!exec) {
+            if (!w.capture && (e = cudaStreamCreateWithFlags(&w.capture, cudaStreamNonBlocking)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamCreate");
+            cudaGraph_t graph = nullptr;
+            if ((e = cudaStreamBeginCapture(w.capture, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamBeginCapture");
+            const cudaError_t le = enqueue(w.capture);
+            e = cudaStreamEndCapture(w.capture, &graph);
+            if (le != cudaSuccess) return cuda_fail(le, "kernel launch (capture)");
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            if (w.graphs.size() >= 8) {
+                cudaGraphExecDestroy(w.graphs.front().exec);
+                w.graphs.erase(w.graphs.begin());
+            }
+            w.graphs.push_back(Workspace::Graph{key, exec});
+        }
+        if ((e = cudaGraphLaunch(exec, s)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    } else {
+        if ((e = enqueue(s)) != cudaSuccess) return cuda_fail(e, "kernel launch");
+    }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     const Ctrl &c = *w.h_ctrl;
     t_stats.part_tasks = static_cast<int64_t>(c.part_tasks);
@@ -433,6 +516,22 @@ int qs_sort_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, qs_stream_t stream)
     return static_cast<int>(run<int32_t>(QS_KIND_KV, d_keys, d_vals, n, 0, 0, stream));
 }
 
+int qs_sort_segmented_i32(int32_t *d_keys, int64_t n, const int64_t *d_offsets, int64_t nseg, qs_stream_t stream)
+{
+    return static_cast<int>(run<int32_t>(QS_KIND_I32, d_keys, nullptr, n, 0, 0, stream, d_offsets, nseg));
+}
+
+int qs_sort_segmented_f64(double *d_keys, int64_t n, const int64_t *d_offsets, int64_t nseg, qs_stream_t stream)
+{
+    return static_cast<int>(run<double>(QS_KIND_F64, d_keys, nullptr, n, 0, 0, stream, d_offsets, nseg));
+}
+
+int qs_sort_segmented_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, const int64_t *d_offsets, int64_t nseg,
+                         qs_stream_t stream)
+{
+    return static_cast<int>(run<int32_t>(QS_KIND_KV, d_keys, d_vals, n, 0, 0, stream, d_offsets, nseg));
+}
+
 int qs_sort_host_i32(int32_t *h_keys, int64_t n, qs_stream_t stream)
 {
     return run_host<int32_t>(QS_KIND_I32, h_keys, nullptr, n, stream);
@@ -499,6 +598,11 @@ int qs_set_option(int option, int64_t value)
     case QS_OPT_DRIVER_CTAS:
         if (value < 0 || value > (1 << 20)) return QS_ERR_INVALID_ARG;
         g_driver_ctas = value;
+        return QS_OK;
+    case QS_OPT_LEAF_MAX:
+    case QS_OPT_SMALL_MAX:
+        if (value < 0 || (value > 0 && (value < 32 || (value & (value - 1))))) return QS_ERR_INVALID_ARG;
+        (option == QS_OPT_LEAF_MAX ? g_leaf_max : g_small_max) = value;
         return QS_OK;
     default:
         return QS_ERR_INVALID_ARG;

@@ -111,13 +111,14 @@ __device__ bool alloc_task(const Args<typename Tr::K, typename Tr::V> &a, int64_
     return true;
 }
 
-// Whole CTA, after alloc_task() and a barrier: makes the task's tickets
-// claimable.
-__device__ __forceinline__ void publish_task(const int32_t *owner_c, const NewTask &nt)
+// Whole CTA (or one warp: first = lane, stride = 32), after alloc_task() and
+// a barrier: makes the task's tickets claimable.
+__device__ __forceinline__ void publish_task(const int32_t *owner_c, const NewTask &nt, int first = -1,
+                                             int stride = kThreads)
 {
     int32_t *owner = const_cast<int32_t *>(owner_c);
     __threadfence();  // order the task's fields (written by thread 0) before its tickets
-    for (long long i = threadIdx.x; i < nt.ntiles; i += kThreads)
+    for (long long i = first < 0 ? threadIdx.x : first; i < nt.ntiles; i += stride)
         asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(owner + nt.g0 + i), "r"(static_cast<int>(nt.id) + 1)
                      : "memory");
 }
@@ -864,7 +865,9 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(Args<typename Tr::K, ty
         __threadfence();
     }
     __syncthreads();
-    if (a.partition_only || a.n > a.leaf_max) {
+    if (a.seg_off) {
+        // Segmented sort: setup_segments_kernel seeds the work.
+    } else if (a.partition_only || a.n > a.leaf_max) {
         uint64_t pbits = a.pivot_bits;
         if (!a.partition_only && tid < 32) pbits = sample_median<K>(a.keys[0], 0, a.n, 0x51ED5EEDull);
         if (tid == 0) {
@@ -875,6 +878,47 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(Args<typename Tr::K, ty
         if (ok) publish_task(a.owner, nt);
     } else if (a.n > 1) {
         if (tid == 0) push_leaf<Tr>(a, 0, a.n, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Segmented sort setup: one warp per segment.  A segment of at most leaf_max
+// keys goes straight to the leaf list; a larger one becomes a partition task
+// with a sampled pivot.  Offsets are checked on the device (0 <= off[i] <=
+// off[i+1] <= n); a bad table records QS_ERR_INVALID_ARG.
+// ---------------------------------------------------------------------------
+template <class Tr>
+__global__ void __launch_bounds__(kThreads) setup_segments_kernel(Args<typename Tr::K, typename Tr::V> a)
+{
+    using K = typename Tr::K;
+    const int lane = threadIdx.x & 31;
+    const long long warp = (static_cast<long long>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
+    const long long nwarps = (static_cast<long long>(gridDim.x) * kThreads) >> 5;
+    for (long long i = warp; i < a.nseg; i += nwarps) {
+        const int64_t off = a.seg_off[i], end = a.seg_off[i + 1];
+        if (off < 0 || end < off || end > a.n) {
+            if (lane == 0) set_error(a.ctrl, -1, static_cast<int>(i));
+            continue;
+        }
+        const int64_t len = end - off;
+        if (len <= 1) continue;
+        if (len <= a.leaf_max) {
+            if (lane == 0) push_leaf<Tr>(a, off, len, 0);
+            continue;
+        }
+        const uint64_t pbits = sample_median<K>(a.keys[0], off, len, static_cast<uint64_t>(off) * 0x9E3779B97F4A7C15ull + len);
+        NewTask nt;
+        int ok = 0;
+        if (lane == 0) {
+            ok = alloc_task<Tr>(a, off, len, 0, pbits, kModeLess, 0, nt);
+            if (ok) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctrl->pending), 1ull);
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) continue;
+        nt.id = __shfl_sync(0xffffffffu, nt.id, 0);
+        nt.g0 = __shfl_sync(0xffffffffu, nt.g0, 0);
+        nt.ntiles = __shfl_sync(0xffffffffu, nt.ntiles, 0);
+        publish_task(a.owner, nt, lane, 32);
     }
 }
 

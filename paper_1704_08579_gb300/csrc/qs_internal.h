@@ -96,6 +96,8 @@ struct Args {
     uint64_t pivot_bits;  // partition-only: the caller's pivot
     int partition_only;
     int profile;  // accumulate per-phase cycle counts into ctrl->cycles
+    const int64_t *seg_off;  // segmented sort: nseg + 1 offsets into keys (nullptr otherwise)
+    int64_t nseg;
 };
 
 // Launch description computed by the host and consumed by the per-kind launchers.
@@ -115,6 +117,7 @@ struct KernelLimits {
 // Per-kind entry points implemented in qs_kind_{i32,f64,kv}.cu.  They enqueue
 // setup + persistent partition kernel + leaf kernel (sort) or setup +
 // persistent kernel (partition only) on cfg.stream and return a cudaError_t.
+// With a.seg_off set they sort every segment [seg_off[i], seg_off[i+1]).
 int launch_i32(const Args<int32_t, int32_t> &a, LaunchCfg &cfg);
 int launch_f64(const Args<double, int32_t> &a, LaunchCfg &cfg);
 int launch_kv(const Args<int32_t, int32_t> &a, LaunchCfg &cfg);

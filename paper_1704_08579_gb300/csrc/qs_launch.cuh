@@ -53,8 +53,12 @@ struct Launcher {
         cudaEvent_t *ev = reinterpret_cast<cudaEvent_t *>(cfg.ev);
         if (cfg.profile) cudaEventRecord(ev[0], s);
         setup_kernel<Tr><<<1, kThreads, 0, s>>>(a);
+        if (a.seg_off) {
+            const long long blocks = (a.nseg + kWarps - 1) / kWarps;
+            setup_segments_kernel<Tr><<<static_cast<int>(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), kThreads, 0, s>>>(a);
+        }
         if (cfg.profile) cudaEventRecord(ev[1], s);
-        if (a.partition_only || a.n > a.leaf_max)
+        if (a.partition_only || a.seg_off || a.n > a.leaf_max)
             driver_kernel<Tr, DriverMin><<<cfg.grid_driver, kThreads, kDriverSmem, s>>>(a);
         if (cfg.profile) cudaEventRecord(ev[2], s);
         if (!a.partition_only) leaf_kernel<Tr, LeafMin><<<cfg.grid_leaf, kThreads, 0, s>>>(a);
