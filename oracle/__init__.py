@@ -62,6 +62,16 @@ def _load():
             lib.oracle_select_i32.restype = i32
             lib.oracle_select_f64.argtypes = [vp, i64, i64]
             lib.oracle_select_f64.restype = f64
+            lib.oracle_mlp_nparams.argtypes = []
+            lib.oracle_mlp_nparams.restype = ctypes.c_long
+            lib.oracle_mlp_forward.argtypes = [vp, vp, ctypes.c_long, vp]
+            lib.oracle_mlp_forward.restype = None
+            lib.oracle_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_long, vp]
+            lib.oracle_mlp_loss_grad.restype = f64
+            for name in ("oracle_bucket_i32", "oracle_bucket_f64"):
+                fn = getattr(lib, name)
+                fn.argtypes = [vp, vp, ctypes.c_long, vp, ctypes.c_int, vp]
+                fn.restype = None
             _lib = lib
     return _lib
 
@@ -141,3 +151,46 @@ def select(keys: np.ndarray, k: int):
     if a.dtype == np.float64:
         return float(lib.oracle_select_f64(_p(a), a.size, int(k)))
     raise TypeError(a.dtype)
+
+
+# ---------------------------------------------------------------------------
+# Learned-splitter growth line: MLP in double precision and bucket partition.
+# ---------------------------------------------------------------------------
+MLP_IN, MLP_HID, MLP_OUT, MLP_SPLIT = 1024, 64, 256, 255
+
+
+def mlp_nparams() -> int:
+    return int(_load().oracle_mlp_nparams())
+
+
+def mlp_forward(params: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """q (batch x 255) for sketches x (batch x 1024)."""
+    lib = _load()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, MLP_IN)
+    q = np.empty((xx.shape[0], MLP_SPLIT), dtype=np.float64)
+    lib.oracle_mlp_forward(_p(p), _p(xx), xx.shape[0], _p(q))
+    return q
+
+
+def mlp_loss_grad(params: np.ndarray, x: np.ndarray, t: np.ndarray):
+    """(loss, gradient) of the mean squared quantile error."""
+    lib = _load()
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, MLP_IN)
+    tt = np.ascontiguousarray(t, dtype=np.float64).reshape(-1, MLP_SPLIT)
+    g = np.empty_like(p)
+    loss = lib.oracle_mlp_loss_grad(_p(p), _p(xx), _p(tt), xx.shape[0], _p(g))
+    return float(loss), g
+
+
+def bucket(keys: np.ndarray, splitters: np.ndarray):
+    """Stable bucket partition: (out, counts) with bucket(k) = #splitters <= k."""
+    lib = _load()
+    k = np.ascontiguousarray(keys)
+    s = np.ascontiguousarray(splitters, dtype=k.dtype)
+    out = np.empty_like(k)
+    counts = np.empty(s.size + 1, dtype=np.int64)
+    fn = lib.oracle_bucket_i32 if k.dtype == np.int32 else lib.oracle_bucket_f64
+    fn(_p(k), _p(out), k.size, _p(s), s.size, _p(counts))
+    return out, counts

@@ -26,9 +26,14 @@
 //       array too.
 //   oracle_select_{i32,f64}        k-th smallest key by repeated Appendix A
 //       steps (quickselect); used to pick a true-median pivot.
+//   oracle_mlp_*, oracle_bucket_*  the learned-splitter growth line (no
+//       counterpart in the paper): the splitter MLP's forward pass and its loss
+//       gradient in double precision, and the 256-way bucket partition by
+//       splitters -- see the section at the end of this file.
 //
 // FP64 keys use IEEE '<' and '=='; inputs hold no NaN and no -0.0.
 #include <cstdint>
+#include <cmath>
 #include <cstdlib>
 
 namespace {
@@ -229,5 +234,173 @@ int oracle_sort_trace_i32(int32_t *a, int64_t n, double *trace, int64_t trace_ca
 int32_t oracle_select_i32(int32_t *a, int64_t n, int64_t k) { return select_kth(a, n, k); }
 
 double oracle_select_f64(double *a, int64_t n, int64_t k) { return select_kth(a, n, k); }
+
+}  // extern "C"
+
+// ===========================================================================
+// Learned splitters (growth line of the method; the paper has no model).
+//
+// Model: x (1024-key sorted sample, min-max scaled to [0,1]) -> h1 = relu(W1 x
+// + b1) (64) -> h2 = relu(W2 h1 + b2) (64) -> z = W3 h2 + b3 (256) -> d =
+// softplus(z) -> c = cumsum(d) -> q_j = c_j / c_255, j = 0..254: 255 monotone
+// quantile estimates in (0, 1).  Loss = mean over the batch and j of
+// (q_j - t_j)^2.  Parameters are one flat array in the order W1 (64x1024,
+// row-major), b1, W2 (64x64), b2, W3 (256x64), b3.
+// ===========================================================================
+namespace {
+constexpr int kIn = 1024, kHid = 64, kOut = 256, kSplit = 255;
+constexpr long kOffW1 = 0, kOffB1 = kOffW1 + long(kHid) * kIn, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + long(kHid) * kHid,
+               kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + long(kOut) * kHid, kNParams = kOffB3 + kOut;
+
+double softplus(double z) { return z > 30.0 ? z : std::log1p(std::exp(z)); }
+double sigmoid(double z) { return 1.0 / (1.0 + std::exp(-z)); }
+
+struct Acts {
+    double a1[kHid], h1[kHid], a2[kHid], h2[kHid], z[kOut], d[kOut], c[kOut], q[kSplit];
+};
+
+void forward_one(const double *p, const double *x, Acts &s)
+{
+    for (int o = 0; o < kHid; ++o) {
+        double acc = p[kOffB1 + o];
+        for (int i = 0; i < kIn; ++i) acc += p[kOffW1 + long(o) * kIn + i] * x[i];
+        s.a1[o] = acc;
+        s.h1[o] = acc > 0 ? acc : 0;
+    }
+    for (int o = 0; o < kHid; ++o) {
+        double acc = p[kOffB2 + o];
+        for (int i = 0; i < kHid; ++i) acc += p[kOffW2 + long(o) * kHid + i] * s.h1[i];
+        s.a2[o] = acc;
+        s.h2[o] = acc > 0 ? acc : 0;
+    }
+    double run = 0;
+    for (int o = 0; o < kOut; ++o) {
+        double acc = p[kOffB3 + o];
+        for (int i = 0; i < kHid; ++i) acc += p[kOffW3 + long(o) * kHid + i] * s.h2[i];
+        s.z[o] = acc;
+        s.d[o] = softplus(acc);
+        run += s.d[o];
+        s.c[o] = run;
+    }
+    for (int j = 0; j < kSplit; ++j) s.q[j] = s.c[j] / s.c[kOut - 1];
+}
+}  // namespace
+
+extern "C" {
+
+long oracle_mlp_nparams(void) { return kNParams; }
+
+// q[b*255 + j] for b < batch.
+void oracle_mlp_forward(const double *params, const double *x, long batch, double *q)
+{
+    Acts s;
+    for (long b = 0; b < batch; ++b) {
+        forward_one(params, x + b * kIn, s);
+        for (int j = 0; j < kSplit; ++j) q[b * kSplit + j] = s.q[j];
+    }
+}
+
+// Loss (mean squared error over batch x 255) and its gradient with respect to
+// every parameter, by the chain rule written out layer by layer.
+double oracle_mlp_loss_grad(const double *params, const double *x, const double *t, long batch, double *grad)
+{
+    const double *p = params;
+    for (long i = 0; i < kNParams; ++i) grad[i] = 0;
+    double loss = 0;
+    const double scale = 1.0 / (double(batch) * kSplit);
+    Acts s;
+    for (long b = 0; b < batch; ++b) {
+        const double *xb = x + b * kIn;
+        const double *tb = t + b * kSplit;
+        forward_one(p, xb, s);
+        double gq[kSplit];
+        for (int j = 0; j < kSplit; ++j) {
+            const double e = s.q[j] - tb[j];
+            loss += e * e * scale;
+            gq[j] = 2.0 * e * scale;
+        }
+        // q_j = c_j / S with S = c_255
+        const double S = s.c[kOut - 1];
+        double gc[kOut];
+        double tail = 0;
+        for (int j = 0; j < kSplit; ++j) {
+            gc[j] = gq[j] / S;
+            tail += gq[j] * s.c[j];
+        }
+        gc[kOut - 1] = -tail / (S * S);
+        // c_k = sum_{i<=k} d_i  =>  gd_i = sum_{k>=i} gc_k
+        double gd[kOut];
+        double acc = 0;
+        for (int i = kOut - 1; i >= 0; --i) {
+            acc += gc[i];
+            gd[i] = acc;
+        }
+        double gz[kOut];
+        for (int i = 0; i < kOut; ++i) gz[i] = gd[i] * sigmoid(s.z[i]);
+        double gh2[kHid] = {0};
+        for (int o = 0; o < kOut; ++o) {
+            grad[kOffB3 + o] += gz[o];
+            for (int i = 0; i < kHid; ++i) {
+                grad[kOffW3 + long(o) * kHid + i] += gz[o] * s.h2[i];
+                gh2[i] += p[kOffW3 + long(o) * kHid + i] * gz[o];
+            }
+        }
+        double ga2[kHid];
+        for (int i = 0; i < kHid; ++i) ga2[i] = s.a2[i] > 0 ? gh2[i] : 0;
+        double gh1[kHid] = {0};
+        for (int o = 0; o < kHid; ++o) {
+            grad[kOffB2 + o] += ga2[o];
+            for (int i = 0; i < kHid; ++i) {
+                grad[kOffW2 + long(o) * kHid + i] += ga2[o] * s.h1[i];
+                gh1[i] += p[kOffW2 + long(o) * kHid + i] * ga2[o];
+            }
+        }
+        for (int o = 0; o < kHid; ++o) {
+            const double ga1 = s.a1[o] > 0 ? gh1[o] : 0;
+            grad[kOffB1 + o] += ga1;
+            for (int i = 0; i < kIn; ++i) grad[kOffW1 + long(o) * kIn + i] += ga1 * xb[i];
+        }
+    }
+    return loss;
+}
+
+// 256-way bucket partition by sorted splitters (nsplit of them, non-decreasing):
+// bucket(k) = number of splitters <= k.  out holds the buckets in order, each
+// keeping input order; counts[b] = keys in bucket b (nsplit + 1 buckets).
+}  // extern "C"
+
+namespace {
+template <class K>
+void bucket_partition(const K *in, K *out, long n, const K *spl, int nsplit, int64_t *counts)
+{
+    for (int b = 0; b <= nsplit; ++b) counts[b] = 0;
+    auto bucket = [&](K k) {
+        int b = 0;
+        while (b < nsplit && !(k < spl[b])) ++b;  // splitter <= key
+        return b;
+    };
+    for (long i = 0; i < n; ++i) counts[bucket(in[i])]++;
+    int64_t *pos = new int64_t[nsplit + 1];
+    int64_t run = 0;
+    for (int b = 0; b <= nsplit; ++b) {
+        pos[b] = run;
+        run += counts[b];
+    }
+    for (long i = 0; i < n; ++i) out[pos[bucket(in[i])]++] = in[i];
+    delete[] pos;
+}
+}  // namespace
+
+extern "C" {
+
+void oracle_bucket_i32(const int32_t *in, int32_t *out, long n, const int32_t *spl, int nsplit, int64_t *counts)
+{
+    bucket_partition(in, out, n, spl, nsplit, counts);
+}
+
+void oracle_bucket_f64(const double *in, double *out, long n, const double *spl, int nsplit, int64_t *counts)
+{
+    bucket_partition(in, out, n, spl, nsplit, counts);
+}
 
 }  // extern "C"
