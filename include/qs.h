@@ -102,6 +102,79 @@ int qs_sort_segmented_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, const int6
                          int64_t nseg, qs_stream_t stream);
 
 /*
+ * Learned splitters (a growth line of the method; the paper has no model).
+ * The sort keeps the paper's method inside every bucket; what is learned is a
+ * set of 255 splitters that cut the array into 256 buckets first:
+ *   1. a sketch: 1024 keys sampled at jittered strides, sorted, min-max scaled
+ *      to [0,1] (qs_sketch_*);
+ *   2. an FP32 MLP 1024 -> 64 (ReLU) -> 64 (ReLU) -> 256 softplus increments,
+ *      whose normalised cumulative sums give 255 monotone positions q in
+ *      [0,1] along the sorted sample; splitter j interpolates linearly between
+ *      the sample keys around position q_j * 1023 (rounded for int32);
+ *   3. a 256-way bucket pass: bucket(k) = number of splitters <= k
+ *      (qs_bucket_* runs it alone, with the caller's splitters);
+ *   4. the plain method on every bucket (the segmented sort).  A bucket that
+ *      comes out larger than 4x its even share is simply split further by the
+ *      plain sampled-median pivots: that is the fallback, and qs_stats reports
+ *      bucket_max / bucket_over as the measure of the model.
+ * The sorted output is the same as qs_sort_*'s (keys bit for bit).
+ *
+ * d_params: device float array of qs_mlp_param_count() parameters laid out as
+ * W1 (64x1024, row-major), b1 (64), W2 (64x64), b2 (64), W3 (256x64), b3
+ * (256); NULL = sampled splitters (every 4th key of the sorted sketch sample),
+ * the same bucket machinery without the model.  Arrays below 2^16 keys use the
+ * plain method.  Synchronous; returns QS_OK or a negative qs_status.
+ */
+int qs_sort_learned_i32(int32_t *d_keys, int64_t n, const float *d_params, qs_stream_t stream);
+int qs_sort_learned_f64(double *d_keys, int64_t n, const float *d_params, qs_stream_t stream);
+
+/*
+ * Bucket pass alone: reorders d_keys[0..n) so that bucket b = the keys with
+ * exactly b of the nsplit (1..255, non-decreasing, device array) splitters <=
+ * key come before bucket b+1; the order inside a bucket is unspecified.
+ * d_bucket_off (device, nsplit + 2 int64) receives the bucket starts and n.
+ * Synchronous; returns QS_OK or a negative qs_status.
+ */
+int qs_bucket_i32(int32_t *d_keys, int64_t n, const int32_t *d_splitters, int nsplit, int64_t *d_bucket_off,
+                  qs_stream_t stream);
+int qs_bucket_f64(double *d_keys, int64_t n, const double *d_splitters, int nsplit, int64_t *d_bucket_off,
+                  qs_stream_t stream);
+
+/*
+ * Sketch of n >= 1024 keys: d_sketch (device, 1024 floats) = the sorted sample
+ * scaled to [0,1], d_minmax (device, 2 doubles) = its smallest and largest
+ * key, d_sample (device, 1024 keys, or NULL) = the sorted sample keys.  This
+ * is the MLP's input.  Synchronous.
+ */
+int qs_sketch_i32(const int32_t *d_keys, int64_t n, float *d_sketch, double *d_minmax, int32_t *d_sample,
+                  qs_stream_t stream);
+int qs_sketch_f64(const double *d_keys, int64_t n, float *d_sketch, double *d_minmax, double *d_sample,
+                  qs_stream_t stream);
+
+/*
+ * Training kernels of the splitter MLP (FP32, all device pointers, asynchronous
+ * on `stream`; they return after enqueueing).
+ *   qs_mlp_param_count  number of parameters (86400).
+ *   qs_mlp_forward      d_x: batch x 1024 sketches -> d_q: batch x 255
+ *                       quantiles; d_act (batch x 640 floats, or NULL) keeps
+ *                       the activations for backward.
+ *   qs_mlp_backward     d_t: batch x 255 targets; gradient of the loss
+ *                       mean((q - t)^2) over batch x 255 into d_grad
+ *                       (param_count floats, overwritten), the loss into
+ *                       *d_loss (or NULL); d_work: batch x 384 floats scratch.
+ *   qs_mlp_adam         one Adam step (beta 0.9/0.999, eps 1e-8, bias
+ *                       corrected; step counts from 1) on d_params with
+ *                       moments d_m, d_v.
+ */
+int qs_mlp_param_count(void);
+int qs_mlp_forward(const float *d_params, const float *d_x, int64_t batch, float *d_q, float *d_act,
+                   qs_stream_t stream);
+int qs_mlp_backward(const float *d_params, const float *d_x, const float *d_t, const float *d_act,
+                    int64_t batch, float *d_work, float *d_grad, float *d_loss, qs_stream_t stream);
+int qs_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int64_t step, float lr,
+                qs_stream_t stream);
+
+/*
  * Host-buffer sorts: h_keys (and h_vals) are HOST pointers (pinned memory is
  * fastest).  The library copies them into a device staging area owned by the
  * workspace, sorts there with the qs_sort_* path, and copies the result back,
@@ -179,6 +252,8 @@ typedef struct {
      * [5] releasing the tile / waiting for the task's other tiles,
      * [6] completing tasks (pivots, children); [7] = tiles processed. */
     int64_t driver_cycles[8];
+    int64_t bucket_max;     /* learned / bucket pass: largest bucket */
+    int64_t bucket_over;    /* learned / bucket pass: buckets above 4x their even share */
 } qs_stats;
 
 int qs_get_stats(qs_stats *out);

@@ -68,6 +68,8 @@ def _load():
             lib.oracle_mlp_forward.restype = None
             lib.oracle_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_long, vp]
             lib.oracle_mlp_loss_grad.restype = f64
+            lib.oracle_adam_step.argtypes = [vp, vp, vp, vp, ctypes.c_long, ctypes.c_long, f64, f64, f64, f64]
+            lib.oracle_adam_step.restype = None
             for name in ("oracle_bucket_i32", "oracle_bucket_f64"):
                 fn = getattr(lib, name)
                 fn.argtypes = [vp, vp, ctypes.c_long, vp, ctypes.c_int, vp]
@@ -194,3 +196,14 @@ def bucket(keys: np.ndarray, splitters: np.ndarray):
     fn = lib.oracle_bucket_i32 if k.dtype == np.int32 else lib.oracle_bucket_f64
     fn(_p(k), _p(out), k.size, _p(s), s.size, _p(counts))
     return out, counts
+
+
+def adam_step(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step on copies; returns (p, m, v)."""
+    lib = _load()
+    p = np.array(p, dtype=np.float64)
+    m = np.array(m, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib.oracle_adam_step(_p(p), _p(g), _p(m), _p(v), p.size, int(step), lr, b1, b2, eps)
+    return p, m, v

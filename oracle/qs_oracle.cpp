@@ -404,3 +404,20 @@ void oracle_bucket_f64(const double *in, double *out, long n, const double *spl,
 }
 
 }  // extern "C"
+
+extern "C" {
+
+// One Adam step (Kingma & Ba 2015): m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+// p -= lr * (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+void oracle_adam_step(double *p, const double *g, double *m, double *v, long n, long step, double lr, double b1,
+                      double b2, double eps)
+{
+    const double c1 = 1.0 - std::pow(b1, double(step)), c2 = 1.0 - std::pow(b2, double(step));
+    for (long i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        p[i] -= lr * (m[i] / c1) / (std::sqrt(v[i] / c2) + eps);
+    }
+}
+
+}  // extern "C"

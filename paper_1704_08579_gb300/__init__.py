@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
         "n", "kind", "part_tasks", "part_keys", "leaf_parts", "leaf_keys", "copy_keys", "max_depth",
         "lookback_words", "grid_driver", "grid_leaf")] + [
         (name, ctypes.c_double) for name in ("ms_driver", "ms_leaf", "ms_copy", "ms_total")] + [
-        ("driver_cycles", ctypes.c_int64 * 8)]
+        ("driver_cycles", ctypes.c_int64 * 8), ("bucket_max", ctypes.c_int64), ("bucket_over", ctypes.c_int64)]
 
 
 def header_functions() -> list[str]:
@@ -79,6 +79,16 @@ def load() -> ctypes.CDLL:
             "qs_sort_segmented_i32": ([vp, i64, vp, i64, vp], ci),
             "qs_sort_segmented_f64": ([vp, i64, vp, i64, vp], ci),
             "qs_sort_segmented_kv": ([vp, vp, i64, vp, i64, vp], ci),
+            "qs_sort_learned_i32": ([vp, i64, vp, vp], ci),
+            "qs_sort_learned_f64": ([vp, i64, vp, vp], ci),
+            "qs_bucket_i32": ([vp, i64, vp, ci, vp, vp], ci),
+            "qs_bucket_f64": ([vp, i64, vp, ci, vp, vp], ci),
+            "qs_sketch_i32": ([vp, i64, vp, vp, vp, vp], ci),
+            "qs_sketch_f64": ([vp, i64, vp, vp, vp, vp], ci),
+            "qs_mlp_param_count": ([], ci),
+            "qs_mlp_forward": ([vp, vp, i64, vp, vp, vp], ci),
+            "qs_mlp_backward": ([vp, vp, vp, vp, i64, vp, vp, vp, vp], ci),
+            "qs_mlp_adam": ([vp, vp, vp, vp, i64, ctypes.c_float, vp], ci),
             "qs_sort_host_i32": ([vp, i64, vp], ci),
             "qs_sort_host_f64": ([vp, i64, vp], ci),
             "qs_sort_host_kv": ([vp, vp, i64, vp], ci),
@@ -195,6 +205,90 @@ def sort_segmented(keys, offsets, values=None, stream=None) -> None:
         _check(lib.qs_sort_segmented_i32(keys.data_ptr(), n, offsets.data_ptr(), nseg, s))
     else:
         _check(lib.qs_sort_segmented_f64(keys.data_ptr(), n, offsets.data_ptr(), nseg, s))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def sort_learned(keys, params=None, stream=None) -> None:
+    """qs_sort_learned_*: 256-way bucket pass by learned (params) or sampled
+    (params=None) splitters, then the plain method in every bucket."""
+    import torch
+
+    lib = load()
+    _check_tensor(keys, "keys")
+    s = _stream_handle(stream)
+    if params is not None:
+        _check_tensor(params, "params")
+        if params.dtype != torch.float32 or params.numel() != lib.qs_mlp_param_count():
+            raise ValueError("params must be %d float32 values" % lib.qs_mlp_param_count())
+    fn = {torch.int32: lib.qs_sort_learned_i32, torch.float64: lib.qs_sort_learned_f64}.get(keys.dtype)
+    if fn is None:
+        raise TypeError("learned sort takes int32 or float64 keys")
+    _check(fn(keys.data_ptr(), keys.numel(), _ptr(params), s))
+
+
+def bucket(keys, splitters, stream=None):
+    """qs_bucket_*: groups keys into nsplit + 1 buckets in place; returns the
+    int64 CUDA tensor of bucket starts (nsplit + 2 entries, last = n)."""
+    import torch
+
+    lib = load()
+    _check_tensor(keys, "keys")
+    _check_tensor(splitters, "splitters")
+    if splitters.dtype != keys.dtype:
+        raise TypeError("splitters must have the keys' dtype")
+    off = torch.empty(splitters.numel() + 2, dtype=torch.int64, device=keys.device)
+    fn = {torch.int32: lib.qs_bucket_i32, torch.float64: lib.qs_bucket_f64}.get(keys.dtype)
+    if fn is None:
+        raise TypeError("bucket pass takes int32 or float64 keys")
+    _check(fn(keys.data_ptr(), keys.numel(), splitters.data_ptr(), splitters.numel(), off.data_ptr(),
+              _stream_handle(stream)))
+    return off
+
+
+def sketch(keys, stream=None):
+    """qs_sketch_*: (sketch float32[1024], minmax float64[2], sorted sample keys[1024]) CUDA tensors."""
+    import torch
+
+    lib = load()
+    _check_tensor(keys, "keys")
+    x = torch.empty(1024, dtype=torch.float32, device=keys.device)
+    mm = torch.empty(2, dtype=torch.float64, device=keys.device)
+    smp = torch.empty(1024, dtype=keys.dtype, device=keys.device)
+    fn = {torch.int32: lib.qs_sketch_i32, torch.float64: lib.qs_sketch_f64}.get(keys.dtype)
+    if fn is None:
+        raise TypeError("sketch takes int32 or float64 keys")
+    _check(fn(keys.data_ptr(), keys.numel(), x.data_ptr(), mm.data_ptr(), smp.data_ptr(), _stream_handle(stream)))
+    return x, mm, smp
+
+
+def mlp_param_count() -> int:
+    return load().qs_mlp_param_count()
+
+
+def mlp_forward(params, x, act=None, stream=None):
+    """q = model(x) for x (batch x 1024, float32 CUDA); act (batch x 640) is filled if given."""
+    import torch
+
+    lib = load()
+    batch = x.shape[0]
+    q = torch.empty(batch, 255, dtype=torch.float32, device=x.device)
+    _check(lib.qs_mlp_forward(params.data_ptr(), x.data_ptr(), batch, q.data_ptr(), _ptr(act), _stream_handle(stream)))
+    return q
+
+
+def mlp_backward(params, x, t, act, work, grad, loss=None, stream=None) -> None:
+    lib = load()
+    _check(lib.qs_mlp_backward(params.data_ptr(), x.data_ptr(), t.data_ptr(), act.data_ptr(), x.shape[0],
+                               work.data_ptr(), grad.data_ptr(), _ptr(loss), _stream_handle(stream)))
+
+
+def mlp_adam(params, grad, m, v, step: int, lr: float, stream=None) -> None:
+    lib = load()
+    _check(lib.qs_mlp_adam(params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), int(step), float(lr),
+                           _stream_handle(stream)))
 
 
 def sort_host(keys, values=None, stream=None) -> None:

@@ -68,6 +68,8 @@ struct Workspace {
     bool dirty = true;  // look-back words / ticket owners must be cleared before use
     cudaEvent_t ev[6] = {};
     cudaStream_t capture = nullptr;  // private stream used to capture CUDA graphs
+    void *aux = nullptr;                   // learned-splitter / bucket state
+    LearnedState *h_learned = nullptr;     // pinned copy of its state
     struct Graph {
         std::string key;
         cudaGraphExec_t exec = nullptr;
@@ -233,7 +235,10 @@ void ws_free(Workspace &w)
     drop_graphs(w);
     if (w.capture) cudaStreamDestroy(w.capture);
     w.capture = nullptr;
-    void *bufs[] = {w.scratch_k, w.scratch_v, w.stage_k, w.stage_v, w.tasks, w.owner, w.pool, w.leaves, w.ctrl};
+    void *bufs[] = {w.scratch_k, w.scratch_v, w.stage_k, w.stage_v, w.tasks, w.owner, w.pool, w.leaves, w.ctrl, w.aux};
+    if (w.h_learned) cudaFreeHost(w.h_learned);
+    w.aux = nullptr;
+    w.h_learned = nullptr;
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (w.h_ctrl) cudaFreeHost(w.h_ctrl);
@@ -267,6 +272,36 @@ const char *status_text(int s)
     case QS_ERR_INTERNAL: return "recursion deeper than the supported limit";
     default: return "device error";
     }
+}
+
+// Kernel arguments for a call on workspace w.
+template <class K>
+Args<K, int32_t> make_args(Workspace &w, int kind, K *keys, int32_t *vals, int64_t n)
+{
+    Args<K, int32_t> a;
+    std::memset(&a, 0, sizeof(a));
+    a.keys[0] = keys;
+    a.keys[1] = static_cast<K *>(w.scratch_k);
+    a.vals[0] = vals;
+    a.vals[1] = kind == QS_KIND_KV ? static_cast<int32_t *>(w.scratch_v) : nullptr;
+    for (int b = 0; b < 2; ++b) {
+        a.key_phase[b] = phase_of<K>(a.keys[b]);
+        a.val_vec[b] = a.vals[b] ? (phase_of<int32_t>(a.vals[b]) == a.key_phase[b]) : 1;
+    }
+    a.n = n;
+    a.tasks = w.tasks;
+    a.owner = w.owner;
+    a.pool = w.pool;
+    a.leaves = w.leaves;
+    a.ctrl = w.ctrl;
+    a.task_cap = w.task_cap;
+    a.pool_cap = w.pool_cap;
+    a.leaf_cap = w.leaf_cap;
+    a.leaf_max = leaf_max_of(kind);
+    a.small_max = small_max_of(kind);
+    a.wait_limit_ns = static_cast<uint64_t>(g_wait_limit_ns.load());
+    a.profile = g_profile.load();
+    return a;
 }
 
 // Runs one sort (partition_only = 0) or partition (1) of kind `kind` on the
@@ -470,6 +505,146 @@ int run_host(int kind, K *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream
     return QS_OK;
 }
 
+constexpr size_t kAuxState = 4096, kAuxSketch = 4096, kAuxSample = 8192, kAuxSpl = 4096;
+constexpr size_t kAuxCnt = sizeof(int64_t) * kLearnedBuckets * kMaxBucketCtas, kAuxAct = 4096;
+constexpr size_t kAuxBytes = kAuxState + kAuxSketch + kAuxSample + kAuxSpl + kAuxCnt + kAuxAct;
+
+int aux_ensure(Workspace &w)
+{
+    if (w.aux) return QS_OK;
+    static_assert(sizeof(LearnedState) <= kAuxState, "state fits its slot");
+    cudaError_t e = cudaMalloc(&w.aux, kAuxBytes);
+    if (e != cudaSuccess) {
+        w.aux = nullptr;
+        return fail(QS_ERR_OOM, "cudaMalloc(learned state): %s", cudaGetErrorString(e));
+    }
+    e = cudaMallocHost(&w.h_learned, sizeof(LearnedState));
+    if (e != cudaSuccess) return fail(QS_ERR_OOM, "cudaMallocHost(learned state): %s", cudaGetErrorString(e));
+    return QS_OK;
+}
+
+LearnedPtrs aux_ptrs(Workspace &w)
+{
+    char *b = static_cast<char *>(w.aux);
+    LearnedPtrs p;
+    p.st = reinterpret_cast<LearnedState *>(b);
+    p.sketch = reinterpret_cast<float *>(b + kAuxState);
+    p.sample = b + kAuxState + kAuxSketch;
+    p.splitters = b + kAuxState + kAuxSketch + kAuxSample;
+    p.cnt = reinterpret_cast<int64_t *>(b + kAuxState + kAuxSketch + kAuxSample + kAuxSpl);
+    p.act = reinterpret_cast<float *>(b + kAuxState + kAuxSketch + kAuxSample + kAuxSpl + kAuxCnt);
+    return p;
+}
+
+// Sketch (op = kOpSketch), bucket pass by the caller's splitters (kOpBucket)
+// or learned / sampled-splitter sort (kOpSortLearned) of i32 or f64 keys.
+template <class K>
+int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const K *user_spl, int nsplit,
+                int64_t *bucket_off_out, float *sketch_out, double *minmax_out, qs_stream_t stream,
+                K *sample_out = nullptr)
+{
+    t_error.clear();
+    std::memset(&t_stats, 0, sizeof(t_stats));
+    t_stats.n = n;
+    t_stats.kind = kind;
+    if (n < 0 || n > kMaxN) return fail(QS_ERR_INVALID_ARG, "n = %lld out of range [0, 2^38]", (long long)n);
+    if (!keys && n > 0) return fail(QS_ERR_INVALID_ARG, "null key pointer");
+    if (reinterpret_cast<uintptr_t>(keys) % sizeof(K)) return fail(QS_ERR_ALIGN, "keys not aligned");
+    if (op == kOpSketch && (n < kLearnedSketch || !sketch_out || !minmax_out))
+        return fail(QS_ERR_INVALID_ARG, "sketch needs n >= 1024 and output pointers");
+    if (op == kOpBucket) {
+        if (nsplit < 1 || nsplit > 255 || !user_spl || !bucket_off_out)
+            return fail(QS_ERR_INVALID_ARG, "bucket pass needs 1..255 splitters and an offsets array");
+        if (n == 0) return QS_OK;
+    }
+    if (op == kOpSortLearned && n < (1 << 16)) {
+        // Too small for 256 buckets to pay: the plain method.
+        return static_cast<int>(run<K>(kind, keys, nullptr, n, 0, 0, stream));
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(QS_ERR_INVALID_ARG, "device %d out of range", dev);
+    Workspace &w = *workspace_for(dev);
+    std::lock_guard<std::mutex> guard(w.mu);
+    int rc = ws_ensure(w, n, kind, kLearnedBuckets);
+    if (rc) return rc;
+    if ((rc = aux_ensure(w))) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (w.dirty) {
+        if ((e = cudaMemsetAsync(w.pool, 0, static_cast<size_t>(w.pool_cap) * 8, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(w.owner, 0, static_cast<size_t>(w.pool_cap) * 4, s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemsetAsync");
+        w.dirty = false;
+    }
+    Args<K, int32_t> a = make_args<K>(w, kind, keys, nullptr, n);
+    LearnedCall lc;
+    std::memset(&lc, 0, sizeof(lc));
+    lc.p = aux_ptrs(w);
+    lc.op = op;
+    lc.params = params;
+    lc.user_spl = user_spl;
+    lc.nsplit = nsplit;
+    lc.ctas = w.sms * 4 < kMaxBucketCtas ? w.sms * 4 : kMaxBucketCtas;
+    lc.bound = 4 * (n / kLearnedBuckets + 1);
+    lc.sketch_out = sketch_out;
+    lc.minmax_out = minmax_out;
+    lc.sample_out = sample_out;
+    LaunchCfg cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.stream = s;
+    const int64_t ctas = g_driver_ctas.load();
+    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][0];
+    cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];
+    cfg.profile = g_profile.load();
+    for (int i = 0; i < 6; ++i) cfg.ev[i] = w.ev[i];
+    int le;
+    if constexpr (sizeof(K) == 8)
+        le = learned_f64(a, lc, cfg);
+    else
+        le = learned_i32(a, lc, cfg);
+    if (le != cudaSuccess) return cuda_fail(static_cast<cudaError_t>(le), "kernel launch");
+    if ((e = cudaMemcpyAsync(w.h_learned, lc.p.st, sizeof(LearnedState), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(w.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(status)");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const LearnedState &ls = *w.h_learned;
+    if (ls.status != 0) return fail(QS_ERR_INTERNAL, "bucket pass index check failed");
+    if (op == kOpSortLearned) {
+        const Ctrl &c = *w.h_ctrl;
+        t_stats.part_tasks = static_cast<int64_t>(c.part_tasks);
+        t_stats.part_keys = static_cast<int64_t>(c.part_keys);
+        t_stats.leaf_parts = static_cast<int64_t>(c.leaf_parts);
+        t_stats.leaf_keys = static_cast<int64_t>(c.leaf_keys);
+        t_stats.copy_keys = static_cast<int64_t>(c.copy_keys);
+        t_stats.max_depth = static_cast<int64_t>(c.max_depth);
+        t_stats.grid_driver = cfg.grid_driver;
+        t_stats.grid_leaf = cfg.grid_leaf;
+        if (c.status != 0) {
+            w.dirty = true;
+            return fail(c.status, "%s (code %d, detail %d)", status_text(c.status), c.status, c.info);
+        }
+        if (cfg.profile) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) t_stats.ms_driver = ms;
+            if (cudaEventElapsedTime(&ms, w.ev[2], w.ev[3]) == cudaSuccess) t_stats.ms_leaf = ms;
+        }
+    }
+    if (op != kOpSketch) {
+        t_stats.bucket_max = static_cast<int64_t>(ls.bucket_max);
+        t_stats.bucket_over = static_cast<int64_t>(ls.bucket_over);
+    }
+    if (op == kOpBucket) {
+        if ((e = cudaMemcpyAsync(keys, w.scratch_k, static_cast<size_t>(n) * sizeof(K), cudaMemcpyDeviceToDevice, s)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(bucket_off_out, lc.p.st->bucket_off, sizeof(int64_t) * (nsplit + 2),
+                                 cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "copy-back");
+    }
+    return QS_OK;
+}
+
 uint64_t bits_i32(int32_t k) { return static_cast<uint64_t>(static_cast<int64_t>(k)); }
 uint64_t bits_f64(double k)
 {
@@ -530,6 +705,75 @@ int qs_sort_segmented_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, const int6
                          qs_stream_t stream)
 {
     return static_cast<int>(run<int32_t>(QS_KIND_KV, d_keys, d_vals, n, 0, 0, stream, d_offsets, nseg));
+}
+
+int qs_sort_learned_i32(int32_t *d_keys, int64_t n, const float *d_params, qs_stream_t stream)
+{
+    return run_learned<int32_t>(QS_KIND_I32, d_keys, n, kOpSortLearned, d_params, nullptr, 0, nullptr, nullptr, nullptr,
+                                stream);
+}
+
+int qs_sort_learned_f64(double *d_keys, int64_t n, const float *d_params, qs_stream_t stream)
+{
+    return run_learned<double>(QS_KIND_F64, d_keys, n, kOpSortLearned, d_params, nullptr, 0, nullptr, nullptr, nullptr,
+                               stream);
+}
+
+int qs_bucket_i32(int32_t *d_keys, int64_t n, const int32_t *d_splitters, int nsplit, int64_t *d_bucket_off,
+                  qs_stream_t stream)
+{
+    return run_learned<int32_t>(QS_KIND_I32, d_keys, n, kOpBucket, nullptr, d_splitters, nsplit, d_bucket_off, nullptr,
+                                nullptr, stream);
+}
+
+int qs_bucket_f64(double *d_keys, int64_t n, const double *d_splitters, int nsplit, int64_t *d_bucket_off,
+                  qs_stream_t stream)
+{
+    return run_learned<double>(QS_KIND_F64, d_keys, n, kOpBucket, nullptr, d_splitters, nsplit, d_bucket_off, nullptr,
+                               nullptr, stream);
+}
+
+int qs_sketch_i32(const int32_t *d_keys, int64_t n, float *d_sketch, double *d_minmax, int32_t *d_sample,
+                  qs_stream_t stream)
+{
+    return run_learned<int32_t>(QS_KIND_I32, const_cast<int32_t *>(d_keys), n, kOpSketch, nullptr, nullptr, 0, nullptr,
+                                d_sketch, d_minmax, stream, d_sample);
+}
+
+int qs_sketch_f64(const double *d_keys, int64_t n, float *d_sketch, double *d_minmax, double *d_sample,
+                  qs_stream_t stream)
+{
+    return run_learned<double>(QS_KIND_F64, const_cast<double *>(d_keys), n, kOpSketch, nullptr, nullptr, 0, nullptr,
+                               d_sketch, d_minmax, stream, d_sample);
+}
+
+int qs_mlp_param_count(void) { return mlp_param_count(); }
+
+int qs_mlp_forward(const float *d_params, const float *d_x, int64_t batch, float *d_q, float *d_act, qs_stream_t stream)
+{
+    t_error.clear();
+    if (batch < 0 || batch > (1 << 20) || !d_params || !d_x || !d_q) return fail(QS_ERR_INVALID_ARG, "bad MLP arguments");
+    const int rc = mlp_forward(d_params, d_x, batch, d_q, d_act, stream);
+    return rc ? cuda_fail(static_cast<cudaError_t>(rc), "MLP forward") : QS_OK;
+}
+
+int qs_mlp_backward(const float *d_params, const float *d_x, const float *d_t, const float *d_act, int64_t batch,
+                    float *d_work, float *d_grad, float *d_loss, qs_stream_t stream)
+{
+    t_error.clear();
+    if (batch < 0 || batch > (1 << 20) || !d_params || !d_x || !d_t || !d_act || !d_work || !d_grad)
+        return fail(QS_ERR_INVALID_ARG, "bad MLP arguments");
+    const int rc = mlp_backward(d_params, d_x, d_t, d_act, batch, d_work, d_grad, d_loss, stream);
+    return rc ? cuda_fail(static_cast<cudaError_t>(rc), "MLP backward") : QS_OK;
+}
+
+int qs_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int64_t step, float lr,
+                qs_stream_t stream)
+{
+    t_error.clear();
+    if (step < 1 || !d_params || !d_grad || !d_m || !d_v) return fail(QS_ERR_INVALID_ARG, "bad Adam arguments");
+    const int rc = mlp_adam(d_params, d_grad, d_m, d_v, step, lr, stream);
+    return rc ? cuda_fail(static_cast<cudaError_t>(rc), "Adam step") : QS_OK;
 }
 
 int qs_sort_host_i32(int32_t *h_keys, int64_t n, qs_stream_t stream)

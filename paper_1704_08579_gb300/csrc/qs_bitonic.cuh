@@ -337,6 +337,9 @@ __device__ __forceinline__ void reg_stage(S (&k)[E], int rb, int mrb, bool tdesc
 template <int E, int LE, class S>
 __device__ void group_bitonic_sort(S (&k)[E], S *sm, int g, int L, int bar, int nthreads)
 {
+    // Every layout used has c == 0 or c >= LE, so LE >= PSH keeps lay_addr's
+    // padding linear in the register index.
+    static_assert(LE >= (sizeof(S) == 8 ? 4 : 5), "too few registers per thread for the padded layouts");
     int cur = 0;
     for (int m = 1; m <= L; ++m) {
         for (int d = m - 1; d >= 0; --d) {

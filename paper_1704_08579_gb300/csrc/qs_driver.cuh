@@ -902,15 +902,17 @@ __global__ void __launch_bounds__(kThreads) setup_segments_kernel(Args<typename 
         }
         const int64_t len = end - off;
         if (len <= 1) continue;
+        const int src = a.seg_src;
         if (len <= a.leaf_max) {
-            if (lane == 0) push_leaf<Tr>(a, off, len, 0);
+            if (lane == 0) push_leaf<Tr>(a, off, len, src ? kLeafScratch : 0);
             continue;
         }
-        const uint64_t pbits = sample_median<K>(a.keys[0], off, len, static_cast<uint64_t>(off) * 0x9E3779B97F4A7C15ull + len);
+        const uint64_t pbits =
+            sample_median<K>(a.keys[src], off, len, static_cast<uint64_t>(off) * 0x9E3779B97F4A7C15ull + len);
         NewTask nt;
         int ok = 0;
         if (lane == 0) {
-            ok = alloc_task<Tr>(a, off, len, 0, pbits, kModeLess, 0, nt);
+            ok = alloc_task<Tr>(a, off, len, src, pbits, kModeLess, 0, nt);
             if (ok) atomicAdd(reinterpret_cast<unsigned long long *>(&a.ctrl->pending), 1ull);
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);

@@ -98,6 +98,7 @@ struct Args {
     int profile;  // accumulate per-phase cycle counts into ctrl->cycles
     const int64_t *seg_off;  // segmented sort: nseg + 1 offsets into keys (nullptr otherwise)
     int64_t nseg;
+    int seg_src;  // buffer holding the segments: 0 caller, 1 scratch
 };
 
 // Launch description computed by the host and consumed by the per-kind launchers.
@@ -107,6 +108,40 @@ struct LaunchCfg {
     int grid_leaf;
     int profile;
     void *ev[6];  // cudaEvent_t when profiling
+};
+
+// Learned-splitter / bucket pass state (one per workspace; device memory).
+constexpr int kLearnedBuckets = 256;
+constexpr int kLearnedSketch = 1024;
+constexpr int kMaxBucketCtas = 2048;
+struct alignas(128) LearnedState {
+    double minmax[2];
+    int64_t bucket_off[kLearnedBuckets + 1];  // bucket starts + total (nsplit + 2 used)
+    unsigned long long bucket_max;
+    unsigned long long bucket_over;  // buckets above the bound
+    int status;
+    int nsplit;
+};
+struct LearnedPtrs {
+    LearnedState *st;
+    float *sketch;     // kLearnedSketch floats
+    void *sample;      // kLearnedSketch sort-space keys (8 bytes each)
+    void *splitters;   // 255 sort-space keys (8 bytes each)
+    int64_t *cnt;      // kLearnedBuckets x kMaxBucketCtas
+    float *act;        // one sample's MLP activations
+};
+enum LearnedOp { kOpSketch = 0, kOpBucket = 1, kOpSortLearned = 2 };
+struct LearnedCall {
+    LearnedPtrs p;
+    int op;
+    const float *params;     // MLP parameters (nullptr = sampled splitters)
+    const void *user_spl;    // kOpBucket: caller's splitters (raw keys)
+    int nsplit;              // kOpBucket: number of caller's splitters (<= 255)
+    int ctas;                // CTAs of the bucket kernels
+    int64_t bound;           // bucket size counted as "over"
+    float *sketch_out;       // kOpSketch outputs (device)
+    double *minmax_out;
+    void *sample_out;        // kOpSketch: sorted sample keys (device, optional)
 };
 
 struct KernelLimits {
@@ -121,6 +156,15 @@ struct KernelLimits {
 int launch_i32(const Args<int32_t, int32_t> &a, LaunchCfg &cfg);
 int launch_f64(const Args<double, int32_t> &a, LaunchCfg &cfg);
 int launch_kv(const Args<int32_t, int32_t> &a, LaunchCfg &cfg);
+// Learned / bucket / sketch operations (i32 and f64 keys).
+int learned_i32(const Args<int32_t, int32_t> &a, const LearnedCall &lc, LaunchCfg &cfg);
+int learned_f64(const Args<double, int32_t> &a, const LearnedCall &lc, LaunchCfg &cfg);
+// MLP kernels (kind-independent).
+int mlp_param_count();
+int mlp_forward(const float *P, const float *X, int64_t batch, float *Q, float *ACT, void *stream);
+int mlp_backward(const float *P, const float *X, const float *T, const float *ACT, int64_t batch, float *WORK,
+                 float *G, float *loss, void *stream);
+int mlp_adam(float *P, const float *G, float *M, float *V, int64_t step, float lr, void *stream);
 KernelLimits limits_i32();
 KernelLimits limits_f64();
 KernelLimits limits_kv();

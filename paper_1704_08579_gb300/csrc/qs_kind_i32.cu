@@ -11,5 +11,6 @@ using L = Launcher<Tr, 3, 2>;
 int launch_i32(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg) { return L::launch(a, cfg); }
 KernelLimits limits_i32() { return L::limits(); }
 int occupancy_i32(int which, int *bps) { return L::occ(which, bps); }
+int learned_i32(const Args<Tr::K, Tr::V> &a, const LearnedCall &lc, LaunchCfg &cfg) { return L::learned(a, lc, cfg); }
 
 }  // namespace qs

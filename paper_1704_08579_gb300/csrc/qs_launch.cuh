@@ -6,6 +6,7 @@
 
 #include "qs_driver.cuh"
 #include "qs_leaf.cuh"
+#include "qs_learned.cuh"
 
 namespace qs {
 
@@ -64,6 +65,33 @@ struct Launcher {
         if (!a.partition_only) leaf_kernel<Tr, LeafMin><<<cfg.grid_leaf, kThreads, 0, s>>>(a);
         if (cfg.profile) cudaEventRecord(ev[3], s);
         return static_cast<int>(cudaGetLastError());
+    }
+    // Sketch / bucket pass / learned sort (keys only).
+    static int learned(const Args<K, V> &a, const LearnedCall &lc, LaunchCfg &cfg)
+    {
+        int rc = prepare();
+        if (rc) return rc;
+        cudaStream_t s = static_cast<cudaStream_t>(cfg.stream);
+        const LearnedBufs<K> lb = bufs_of<K>(lc.p);
+        sketch_kernel<K><<<1, 256, 0, s>>>(a.keys[0], a.n, lb, lc.sketch_out, lc.minmax_out, static_cast<K *>(lc.sample_out));
+        if (lc.op == kOpSketch) return static_cast<int>(cudaGetLastError());
+        int nsplit = 255;
+        if (lc.op == kOpBucket) {
+            nsplit = lc.nsplit;
+            splitters_from_keys_kernel<K><<<1, 256, 0, s>>>(static_cast<const K *>(lc.user_spl), nsplit, lb);
+        } else {
+            splitter_kernel<K><<<1, 256, 0, s>>>(lc.params, lb);
+        }
+        bucket_hist_kernel<Tr><<<lc.ctas, kThreads, 0, s>>>(a.keys[0], a.n, lb, nsplit);
+        bucket_scan_kernel<<<1, 1024, 0, s>>>(lb.cnt, lc.ctas, lb.st, nsplit, a.n, lc.bound);
+        bucket_scatter_kernel<Tr><<<lc.ctas, kThreads, 0, s>>>(a, lb, nsplit);
+        if (lc.op == kOpBucket) return static_cast<int>(cudaGetLastError());
+        // Every bucket is then sorted by the plain method, straight from scratch.
+        Args<K, V> a2 = a;
+        a2.seg_off = lb.st->bucket_off;
+        a2.nseg = kBuckets;
+        a2.seg_src = 1;
+        return launch(a2, cfg);
     }
 };
 

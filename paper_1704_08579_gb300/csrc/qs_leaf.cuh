@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
     if (tid == 0) sm.has_carry = 0;
     // Large parts: thread 0 packs parts into thread groups (32 .. kThreads
     // threads each, E keys per thread); a part that does not fit is carried
-    // over to this CTA's next round.
+    // over to this CTA's next pass.
     for (;;) {
         if (tid == 0) {
             int ng = 0, used = 0;

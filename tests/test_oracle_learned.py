@@ -99,3 +99,18 @@ def test_bucket_partition(dtype):
     b = np.searchsorted(spl, x, side="right")
     np.testing.assert_array_equal(counts, np.bincount(b, minlength=256))
     np.testing.assert_array_equal(out, x[np.argsort(b, kind="stable")])
+
+
+def test_adam_first_step_closed_form():
+    """At step 1 with zero moments the bias-corrected update is lr * g / (|g| + eps)."""
+    rng = np.random.default_rng(14)
+    p = rng.normal(size=1000)
+    g = rng.normal(size=1000)
+    z = np.zeros(1000)
+    p1, m1, v1 = oracle.adam_step(p, g, z, z, 1, 0.01)
+    np.testing.assert_allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(m1, 0.1 * g, rtol=1e-14)
+    np.testing.assert_allclose(v1, 0.001 * g * g, rtol=1e-12)
+    # a second step with the same gradient keeps moving the same way
+    p2, _, _ = oracle.adam_step(p1, g, m1, v1, 2, 0.01)
+    assert np.all(np.sign(p1 - p2) == np.sign(g))
