@@ -324,6 +324,7 @@ def run_ours(args):
         if not args.no_extra:
             line["extra"] = _extras(torch, qs, stream, hbm_peak)
             line["batched"] = _batched(torch, qs, stream)
+            line["learned"] = _learned(torch, qs, stream)
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_oracle_baseline()
         print(json.dumps(line), flush=True)
@@ -403,6 +404,71 @@ def _batched(torch, qs, stream, nseg=20_000, steps=3):
     return out
 
 
+def _learned(torch, qs, stream, steps=3):
+    """Learned-splitter form on the skewed workloads: 2^30 int32 keys Zipf(1.2)
+    over 2^24 values, 2^30 int32 keys from an 8-Gaussian mixture, 2^28 FP64
+    keys lognormal(0, 2).  The network is first trained (untimed) on
+    sort-generated pairs with the library's kernels; then the plain sort, the
+    bucket form with sampled splitters and the learned form are timed on the
+    same array (median of `steps`), and the bucket forms' outputs are checked
+    equal to the plain sort's."""
+    import synth.device as sdev
+    from paper_1704_08579_gb300 import learned
+
+    models, train_s = {}, {}
+    for kind in ("i32", "f64"):
+        t0 = time.perf_counter()
+        X, T = learned.training_set(kind, 4096, 1 << 16, seed=7)
+        models[kind], _ = learned.train(X, T, steps=3000, batch=128, lr=3e-4, seed=3)
+        torch.cuda.synchronize()
+        train_s[kind] = time.perf_counter() - t0
+        del X, T
+    out = {"train_seconds": train_s}
+    cases = (("zipf_i32_2^30", "i32", lambda: sdev.zipf_i32(1 << 30)),
+             ("gauss_mix8_i32_2^30", "i32", lambda: sdev.gauss_mix_i32(1 << 30)),
+             ("lognormal_f64_2^28", "f64", lambda: sdev.lognormal_f64(1 << 28)))
+    for name, kind, make in cases:
+        pristine = make()
+        n = pristine.numel()
+        work = torch.empty_like(pristine)
+        ref = None
+        res = {}
+        for arm in ("plain", "sampled", "learned"):
+            times, st = [], None
+            for r in range(steps + 1):
+                work.copy_(pristine)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    a.record(stream)
+                    if arm == "plain":
+                        qs.sort(work, stream=stream)
+                    else:
+                        qs.sort_learned(work, models[kind] if arm == "learned" else None, stream=stream)
+                    b.record(stream)
+                b.synchronize()
+                st = qs.stats()
+                if r:
+                    times.append(a.elapsed_time(b))
+            ms = statistics.median(times)
+            res[arm] = {"ms": ms, "gkeys_s": n / (ms / 1e3) / 1e9}
+            if arm == "plain":
+                ref = work.clone()
+                res[arm]["sorted"] = bool((ref[1:] >= ref[:-1]).all())
+            else:
+                res[arm].update({"imbalance_err": st["bucket_dev"] / (2.0 * n * 256),
+                                 "bucket_max_over_even": st["bucket_max"] / (n / 256.0),
+                                 "buckets_over_bound": st["bucket_over"],
+                                 "equal_to_plain": bool(torch.equal(work.view(torch.int64) if kind == "f64" else work,
+                                                                    ref.view(torch.int64) if kind == "f64" else ref))})
+        res["n"] = n
+        out[name] = res
+        del pristine, work, ref
+        torch.cuda.empty_cache()
+    return out
+
+
 def _extras(torch, qs, stream, hbm_peak):
     out = []
     n = N_KEYS
@@ -473,8 +539,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--op", choices=["sort", "partition"], default="sort",
-                    help="partition: time qs_partition_f64 alone (profiling aid; not the benchmark line)")
+    ap.add_argument("--op", choices=["sort", "partition", "learned", "batched"], default="sort",
+                    help="partition / learned / batched: that measurement alone (not the benchmark line)")
     ap.add_argument("--log2n", type=int, default=LOG2N,
                     help="log2 of the keys per sort (28 = the benchmark workload; smaller only for profiling)")
     args = ap.parse_args()
@@ -486,7 +552,25 @@ def main():
         return run_reference(args)
     if args.op == "partition":
         return run_partition_only(args)
+    if args.op in ("learned", "batched"):
+        return run_section(args.op)
     return run_ours(args)
+
+
+def run_section(name: str) -> int:
+    """One secondary measurement alone, printed as its own JSON line."""
+    import torch
+
+    import paper_1704_08579_gb300 as qs
+    from paper_1704_08579_gb300 import build as qs_build
+
+    torch.cuda.set_device(0)
+    qs_build.build()
+    qs.load()
+    stream = torch.cuda.Stream()
+    res = _learned(torch, qs, stream) if name == "learned" else _batched(torch, qs, stream)
+    print(json.dumps({"section": name, name: res}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

@@ -254,6 +254,9 @@ typedef struct {
     int64_t driver_cycles[8];
     int64_t bucket_max;     /* learned / bucket pass: largest bucket */
     int64_t bucket_over;    /* learned / bucket pass: buckets above 4x their even share */
+    int64_t bucket_dev;     /* learned / bucket pass: sum over the B buckets of |size * B - n|;
+                               bucket_dev / (2 n B) is the imbalance error (total variation
+                               distance between the bucket sizes and an even split) */
 } qs_stats;
 
 int qs_get_stats(qs_stats *out);

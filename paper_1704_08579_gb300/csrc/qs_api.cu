@@ -555,7 +555,11 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     if (op == kOpBucket) {
         if (nsplit < 1 || nsplit > 255 || !user_spl || !bucket_off_out)
             return fail(QS_ERR_INVALID_ARG, "bucket pass needs 1..255 splitters and an offsets array");
-        if (n == 0) return QS_OK;
+        if (n == 0) {  // every bucket starts (and ends) at 0
+            const cudaError_t e0 = cudaMemsetAsync(bucket_off_out, 0, sizeof(int64_t) * (nsplit + 2),
+                                                   reinterpret_cast<cudaStream_t>(stream));
+            return e0 == cudaSuccess ? QS_OK : cuda_fail(e0, "cudaMemsetAsync");
+        }
     }
     if (op == kOpSortLearned && n < (1 << 16)) {
         // Too small for 256 buckets to pay: the plain method.
@@ -633,6 +637,7 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     if (op != kOpSketch) {
         t_stats.bucket_max = static_cast<int64_t>(ls.bucket_max);
         t_stats.bucket_over = static_cast<int64_t>(ls.bucket_over);
+        t_stats.bucket_dev = static_cast<int64_t>(ls.bucket_dev);
     }
     if (op == kOpBucket) {
         if ((e = cudaMemcpyAsync(keys, w.scratch_k, static_cast<size_t>(n) * sizeof(K), cudaMemcpyDeviceToDevice, s)) !=

@@ -901,8 +901,14 @@ __global__ void __launch_bounds__(kThreads) setup_segments_kernel(Args<typename 
             continue;
         }
         const int64_t len = end - off;
-        if (len <= 1) continue;
         const int src = a.seg_src;
+        if (len <= 1) {  // already sorted; from scratch it only has to move home
+            if (len == 1 && src && lane == 0) {
+                a.keys[0][off] = a.keys[1][off];
+                if constexpr (Tr::KV) a.vals[0][off] = a.vals[1][off];
+            }
+            continue;
+        }
         if (len <= a.leaf_max) {
             if (lane == 0) push_leaf<Tr>(a, off, len, src ? kLeafScratch : 0);
             continue;

@@ -119,6 +119,7 @@ struct alignas(128) LearnedState {
     int64_t bucket_off[kLearnedBuckets + 1];  // bucket starts + total (nsplit + 2 used)
     unsigned long long bucket_max;
     unsigned long long bucket_over;  // buckets above the bound
+    unsigned long long bucket_dev;   // sum over buckets of |size * nbuckets - n|
     int status;
     int nsplit;
 };

@@ -2,9 +2,9 @@
 //   sketch_kernel    1024 keys sampled at jittered strides, sorted with the
 //                    Bitonic group network, min-max scaled to [0,1] (FP32);
 //   splitter_kernel  255 splitters: the MLP's monotone quantile positions
-//                    along the sorted sample, mapped back to keys by
-//                    interpolating between sample keys (learned), or every
-//                    4th sorted sample key (sampled);
+//                    along the sorted sample's moving-average curve, mapped
+//                    back to keys by interpolating between curve points
+//                    (learned), or every 4th sorted sample key (sampled);
 //   bucket_hist / bucket_scan / bucket_scatter
 //                    256-way partition by the splitters: bucket(k) = number
 //                    of splitters <= k (binary search in shared memory);
@@ -111,31 +111,52 @@ __global__ void __launch_bounds__(256) sketch_kernel(const K *__restrict__ keys,
     }
 }
 
-// Splitter j from quantile position q in [0,1] along the sorted sample:
-// linear interpolation between the neighbouring sample keys, rounded to the
-// key type.
+// The curve the model's positions are read on: the sorted sample smoothed by
+// a centred moving average over kCurveW keys (the window shrinks
+// symmetrically at both ends, so the first and last keys stay the sample's
+// minimum and maximum).  A moving average of a sorted sequence is
+// non-decreasing.  The sample's own bucket noise (about four sample keys per
+// bucket) is high-frequency; the network's output, a 64-wide bottleneck,
+// can only move the splitters smoothly, so it works on a curve from which
+// that noise is already averaged out.
+constexpr int kCurveHalf = 8, kCurveW = 2 * kCurveHalf + 1;
+
 template <class K>
-__device__ __forceinline__ K key_at_position(const typename KeyOps<K>::S *sample, float q)
+__device__ __forceinline__ void sample_curve(const typename KeyOps<K>::S *sample, double *curve)
 {
     using Ops = KeyOps<K>;
+    for (int i = threadIdx.x; i < kSketchN; i += blockDim.x) {
+        const int lo = i - kCurveHalf < 0 ? 0 : i - kCurveHalf;
+        const int hi = i + kCurveHalf > kSketchN - 1 ? kSketchN - 1 : i + kCurveHalf;
+        const int h = (i - lo) < (hi - i) ? (i - lo) : (hi - i);
+        double s = 0;
+        for (int k = i - h; k <= i + h; ++k) s += static_cast<double>(Ops::from_s(sample[k]));
+        curve[i] = s / (2 * h + 1);
+    }
+}
+
+// Splitter from quantile position q in [0,1] along the curve: linear
+// interpolation between neighbouring curve points, rounded to the key type.
+template <class K>
+__device__ __forceinline__ K key_at_position(const double *curve, float q)
+{
     const double p = static_cast<double>(q < 0.f ? 0.f : (q > 1.f ? 1.f : q)) * (kSketchN - 1);
-    int i = static_cast<int>(p);
-    if (i >= kSketchN - 1) return Ops::from_s(sample[kSketchN - 1]);
-    const double f = p - i;
-    const double a = static_cast<double>(Ops::from_s(sample[i]));
-    const double b = static_cast<double>(Ops::from_s(sample[i + 1]));
-    const double v = a + f * (b - a);
+    const int i = static_cast<int>(p);
+    if (i >= kSketchN - 1) return static_cast<K>(curve[kSketchN - 1]);
+    const double a = curve[i], b = curve[i + 1];
+    double v = a + (p - i) * (b - a);
+    v = v < a ? a : (v > b ? b : v);
     if constexpr (sizeof(K) == 4) {
-        const double r = rint(v);
-        return static_cast<K>(static_cast<long long>(r < a ? a : (r > b ? b : r)));
+        const double r = rint(v);  // between two int32 means: stays in range
+        return static_cast<K>(static_cast<long long>(r));
     } else {
-        return v < a ? a : (v > b ? b : v);
+        return v;
     }
 }
 
 // Splitters: learned (params != nullptr) or sampled.  One CTA of 256 threads.
-// The model's q_j is a position along the sorted sample; the sampled form
-// takes every 4th sample key.
+// The model's q_j is a position along the smoothed sample curve; the sampled
+// form takes every 4th sample key.
 template <class K>
 __global__ void __launch_bounds__(256) splitter_kernel(const float *__restrict__ params, LearnedBufs<K> lb)
 {
@@ -143,12 +164,14 @@ __global__ void __launch_bounds__(256) splitter_kernel(const float *__restrict__
     using S = typename Ops::S;
     __shared__ mlp::Smem sm;
     __shared__ S spl[mlp::kSplit];
+    __shared__ double curve[kSketchN];
     const int t = threadIdx.x;
     if (params) {
         for (int i = t; i < kSketchN; i += 256) sm.x[i] = lb.sketch[i];
+        sample_curve<K>(lb.sample, curve);
         __syncthreads();
         mlp::forward_cta(params, sm);
-        if (t < mlp::kSplit) spl[t] = Ops::to_s(key_at_position<K>(lb.sample, sm.c[t] / sm.c[mlp::kOut - 1]));
+        if (t < mlp::kSplit) spl[t] = Ops::to_s(key_at_position<K>(curve, sm.c[t] / sm.c[mlp::kOut - 1]));
     } else if (t < mlp::kSplit) {
         spl[t] = lb.sample[4 * (t + 1)];
     }
@@ -249,14 +272,17 @@ static __global__ void __launch_bounds__(1024) bucket_scan_kernel(int64_t *__res
     __syncthreads();
     if (t == 0) {
         st->bucket_off[nsplit + 1] = n;
-        unsigned long long mx = 0, over = 0;
+        unsigned long long mx = 0, over = 0, dev = 0;
         for (int b = 0; b <= nsplit; ++b) {
             const unsigned long long sz = static_cast<unsigned long long>(st->bucket_off[b + 1] - st->bucket_off[b]);
             mx = sz > mx ? sz : mx;
             over += sz > static_cast<unsigned long long>(bound) ? 1 : 0;
+            const long long d = static_cast<long long>(sz) * (nsplit + 1) - n;  // vs the even share n/(nsplit+1)
+            dev += static_cast<unsigned long long>(d < 0 ? -d : d);
         }
         st->bucket_max = mx;
         st->bucket_over = over;
+        st->bucket_dev = dev;
     }
 }
 

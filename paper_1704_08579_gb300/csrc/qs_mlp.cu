@@ -1,4 +1,6 @@
 // Host launchers of the splitter-MLP kernels (kind-independent).
+#include <cmath>
+
 #include "qs_mlp.cuh"
 
 namespace qs {
@@ -126,15 +128,18 @@ __global__ void backward_param_kernel(const float *__restrict__ X, const float *
     G[p] = acc;
 }
 
-// Adam (Kingma & Ba 2015) with bias correction; step counts from 1.
+// Adam (Kingma & Ba 2015) with bias correction; step counts from 1.  The
+// decay weights and both (1 - beta) factors come from the host, computed in
+// double: 1 - 0.999f alone would be off by 1.3e-5 relative.
 __global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ G, float *__restrict__ M,
-                            float *__restrict__ V, float lr, float b1, float b2, float eps, float c1, float c2)
+                            float *__restrict__ V, float lr, float b1, float omb1, float b2, float omb2, float eps,
+                            float c1, float c2)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= kNParams) return;
     const float g = G[p];
-    const float m = b1 * M[p] + (1.f - b1) * g;
-    const float v = b2 * V[p] + (1.f - b2) * g * g;
+    const float m = b1 * M[p] + omb1 * g;
+    const float v = b2 * V[p] + omb2 * g * g;
     M[p] = m;
     V[p] = v;
     P[p] -= lr * (m / c1) / (sqrtf(v / c2) + eps);
@@ -164,11 +169,12 @@ int mlp_backward(const float *P, const float *X, const float *T, const float *AC
 
 int mlp_adam(float *P, const float *G, float *M, float *V, int64_t step, float lr, void *stream)
 {
-    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-    const float c1 = 1.f - powf(b1, static_cast<float>(step));
-    const float c2 = 1.f - powf(b2, static_cast<float>(step));
-    mlp::adam_kernel<<<(mlp::kNParams + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(P, G, M, V, lr, b1, b2,
-                                                                                                  eps, c1, c2);
+    const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+    const double c1 = 1.0 - std::pow(b1, static_cast<double>(step));
+    const double c2 = 1.0 - std::pow(b2, static_cast<double>(step));
+    mlp::adam_kernel<<<(mlp::kNParams + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        P, G, M, V, lr, static_cast<float>(b1), static_cast<float>(1.0 - b1), static_cast<float>(b2),
+        static_cast<float>(1.0 - b2), static_cast<float>(eps), static_cast<float>(c1), static_cast<float>(c2));
     return static_cast<int>(cudaGetLastError());
 }
 

@@ -4,15 +4,16 @@ The network is trained on (sketch, exact quantile) pairs that the sort itself
 generates: for each training array the library computes the 1024-key sketch
 (qs_sketch_*) and sorts the array (qs_sort_*); the targets are the keys at
 ranks floor((j+1) n / 256), j = 0..254, of the sorted array, expressed as
-positions along the sorted sample (the space the model predicts in: a key that
-occurs in the sample maps to the middle of its run there, a key between two
-sample keys to the linear interpolation between their positions).  The
+positions along the curve the sort reads the model's output on -- the sorted
+sample smoothed by a 17-key centred moving average (a key between two curve
+points maps to the linear interpolation between their positions, a key equal
+to a run of curve points to the run's middle).  The
 forward, backward and Adam steps are the library's own kernels
 (qs_mlp_forward / qs_mlp_backward / qs_mlp_adam); torch only holds buffers and
 draws the training arrays.
 
-The untrained network (last layer zero) outputs q_j = (j+1)/256, i.e. the
-sampled splitters; training moves it from there.
+The untrained network (last layer zero) outputs q_j = (j+1)/256: evenly
+spaced positions on the curve; training moves it from there.
 """
 from __future__ import annotations
 
@@ -79,20 +80,35 @@ def draw_array(kind: str, family: str, n: int, gen):
 FAMILIES = {"i32": ("zipf", "gmix", "normal", "uniform"), "f64": ("lognormal", "gmix", "normal", "uniform")}
 
 
-def positions(sample, v):
-    """Positions in [0, 1023] of values v along the sorted sample (see module doc)."""
+CURVE_HALF = 8  # moving-average half window of the curve the positions are read on
+
+
+def curve(sample):
+    """The sorted sample smoothed by a centred moving average over 17 keys,
+    the window shrinking symmetrically at both ends (float64)."""
     torch = _torch()
     s = sample.to(torch.float64)
+    m = s.numel()
+    c = torch.cat([torch.zeros(1, dtype=torch.float64, device=s.device), torch.cumsum(s, 0)])
+    i = torch.arange(m, device=s.device)
+    h = torch.minimum(torch.minimum(i, m - 1 - i), torch.full_like(i, CURVE_HALF))
+    return (c[i + h + 1] - c[i - h]) / (2 * h + 1).to(torch.float64)
+
+
+def positions(cv, v):
+    """Positions in [0, 1023] of values v along the non-decreasing curve cv
+    (the middle of a run of equal curve points, else linear interpolation)."""
+    torch = _torch()
     vv = v.to(torch.float64)
-    a = torch.searchsorted(s, vv, side="left")
-    b = torch.searchsorted(s, vv, side="right")
+    a = torch.searchsorted(cv, vv, side="left")
+    b = torch.searchsorted(cv, vv, side="right")
     present = a < b
-    lo = (a - 1).clamp(0, 1022)
-    sl, sh = s[lo], s[lo + 1]
+    lo = (a - 1).clamp(0, cv.numel() - 2)
+    sl, sh = cv[lo], cv[lo + 1]
     frac = torch.where(sh > sl, (vv - sl) / (sh - sl), torch.zeros_like(vv)).clamp(0, 1)
     p = torch.where(present, (a + b - 1).to(torch.float64) / 2, lo.to(torch.float64) + frac)
-    p = torch.where(vv < s[0], torch.zeros_like(p), p)
-    p = torch.where(vv > s[-1], torch.full_like(p, 1023.0), p)
+    p = torch.where(vv < cv[0], torch.zeros_like(p), p)
+    p = torch.where(vv > cv[-1], torch.full_like(p, cv.numel() - 1.0), p)
     return p
 
 
@@ -105,7 +121,7 @@ def pair(keys):
     qs.sort(srt)
     n = keys.numel()
     ranks = torch.tensor([((j + 1) * n) // 256 for j in range(NQ)], device=keys.device)
-    t = positions(sample, srt[ranks]) / 1023.0
+    t = positions(curve(sample), srt[ranks]) / 1023.0
     return x, t.to(torch.float32)
 
 
@@ -169,16 +185,43 @@ def train(X, T, steps: int = 1500, batch: int = 128, lr: float = 2e-3, seed: int
     return p, losses
 
 
-def imbalance(keys, params=None) -> float:
-    """Largest bucket / (n / 256) when `keys` (not modified) is cut by learned
-    (params) or sampled (None) splitters: the balance the per-bucket sorts
-    then see."""
-    torch = _torch()
+def imbalance(keys, params=None) -> dict:
+    """Bucket balance when `keys` (not modified) is cut by learned (params) or
+    sampled (None) splitters, as the bucket pass of the sort reports it:
+    err = total variation distance between the bucket sizes and an even split
+    (0 = perfect), max = largest bucket / even share, over = buckets above the
+    fallback bound."""
     work = keys.clone()
     qs.sort_learned(work, params)
     st = qs.stats()
     del work
-    return st["bucket_max"] / (keys.numel() / 256.0)
+    n = keys.numel()
+    return {"err": st["bucket_dev"] / (2.0 * n * 256), "max": st["bucket_max"] / (n / 256.0), "over": st["bucket_over"]}
+
+
+def position_error(params, X, T) -> float:
+    """Mean squared error of the model's positions against the targets."""
+    q = qs.mlp_forward(params, X)
+    return float(((q - T) ** 2).mean().item())
+
+
+def compare(params, kind: str, count: int, n: int, seed: int) -> dict:
+    """Mean bucket-imbalance error per family on fresh arrays: the trained
+    model (params), the untrained one (even positions on the curve) and the
+    sampled splitters (every 4th sample key)."""
+    torch = _torch()
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    init = init_params(0)
+    fams = FAMILIES[kind]
+    out = {f: {"learned": [], "untrained": [], "sampled": []} for f in fams}
+    for i in range(count):
+        f = fams[i % len(fams)]
+        keys = draw_array(kind, f, n, gen)
+        out[f]["learned"].append(imbalance(keys, params)["err"])
+        out[f]["untrained"].append(imbalance(keys, init)["err"])
+        out[f]["sampled"].append(imbalance(keys, None)["err"])
+    return {f: {k: sum(v) / len(v) for k, v in d.items()} for f, d in out.items()}
 
 
 def save(params, path: str) -> None:

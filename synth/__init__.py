@@ -175,9 +175,7 @@ def _normal(seed: int, a: int, b: int) -> np.ndarray:
 def zipf_i32(n: int, seed: int | None = None, s: float = 1.2, nvals: int = 1 << 24) -> np.ndarray:
     """Zipf(s) ranks over 1..nvals by inverse CDF, mapped by a seeded bijection onto {k*256 - 2^31}."""
     seed = SEEDS["c5_zipf_i32"] if seed is None else seed
-    w = np.arange(1, nvals + 1, dtype=np.float64) ** (-s)
-    cdf = np.cumsum(w)
-    cdf /= cdf[-1]
+    cdf = zipf_cdf(s, nvals)
     mult = np.int64(2654435761 | 1) % np.int64(nvals)  # odd => bijection mod 2^24
     out = np.empty(n, dtype=np.int32)
     for a, b in _chunks(n):
@@ -188,20 +186,32 @@ def zipf_i32(n: int, seed: int | None = None, s: float = 1.2, nvals: int = 1 << 
     return out
 
 
-def gauss_mix_i32(n: int, seed: int | None = None, k: int = 8) -> np.ndarray:
-    """Mixture of k Gaussians (means U[-1.5e9, 1.5e9], sigma log-U[1e5, 1e8]), rounded, clipped to int32."""
-    seed = SEEDS["c5_gmix_i32"] if seed is None else seed
+def gauss_mix_params(seed: int, k: int = 8):
+    """Component means U[-1.5e9, 1.5e9], sigmas log-U[1e5, 1e8] and cumulative weights of the mixture."""
     p = _u53(splitmix64(seed ^ 0xC0FFEE, 0, 3 * k))
     means = -1.5e9 + 3e9 * p[:k]
     sig = np.exp(np.log(1e5) + (np.log(1e8) - np.log(1e5)) * p[k:2 * k])
     wts = 0.5 + p[2 * k:]
-    cw = np.cumsum(wts / wts.sum())
+    return means, sig, np.cumsum(wts / wts.sum())
+
+
+def gauss_mix_i32(n: int, seed: int | None = None, k: int = 8) -> np.ndarray:
+    """Mixture of k Gaussians (means U[-1.5e9, 1.5e9], sigma log-U[1e5, 1e8]), rounded, clipped to int32."""
+    seed = SEEDS["c5_gmix_i32"] if seed is None else seed
+    means, sig, cw = gauss_mix_params(seed, k)
     out = np.empty(n, dtype=np.int32)
     for a, b in _chunks(n):
         comp = np.minimum(np.searchsorted(cw, _u53(splitmix64(seed ^ 0xA11, a, b - a)), side="right"), k - 1)
         x = np.rint(means[comp] + sig[comp] * _normal(seed, a, b))
         out[a:b] = np.clip(x, -2147483648.0, 2147483647.0).astype(np.int32)
     return out
+
+
+def zipf_cdf(s: float = 1.2, nvals: int = 1 << 24) -> np.ndarray:
+    w = np.arange(1, nvals + 1, dtype=np.float64) ** (-s)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    return cdf
 
 
 def lognormal_f64(n: int, seed: int | None = None, sigma: float = 2.0) -> np.ndarray:
