@@ -249,9 +249,13 @@ typedef struct {
     /* Profiling on: SM clock cycles the persistent kernel's CTAs spent, summed
      * over CTAs, in [0] waiting for work, [1] waiting for a tile's keys,
      * [2] comparing and counting, [3] the look-back, [4] staging and storing,
-     * [5] releasing the tile / waiting for the task's other tiles,
-     * [6] completing tasks (pivots, children); [7] = tiles processed. */
-    int64_t driver_cycles[8];
+     * [5] releasing the tile, [6] completing tasks (pivots, children);
+     * [7] = tiles processed; [8] cycles inside the look-back proper (warp 0),
+     * [9] cycles warps 1..7 waited for the prefetched tile, [10] look-back
+     * windows of 32 words read, [11] re-reads of unpublished words;
+     * [13] claiming and resolving the next ticket and issuing its load
+     * (thread 0); [12], [14], [15] unused. */
+    int64_t driver_cycles[16];
     int64_t bucket_max;     /* learned / bucket pass: largest bucket */
     int64_t bucket_over;    /* learned / bucket pass: buckets above 4x their even share */
     int64_t bucket_dev;     /* learned / bucket pass: sum over the B buckets of |size * B - n|;

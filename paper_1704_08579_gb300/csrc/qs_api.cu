@@ -438,7 +438,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     t_stats.lookback_words = static_cast<int64_t>(c.pool_cursor);
     t_stats.grid_driver = cfg.grid_driver;
     t_stats.grid_leaf = cfg.grid_leaf;
-    for (int i = 0; i < 8; ++i) t_stats.driver_cycles[i] = static_cast<int64_t>(c.cycles[i]);
+    for (int i = 0; i < kProfSlots; ++i) t_stats.driver_cycles[i] = static_cast<int64_t>(c.cycles[i]);
     if (c.status != 0) {
         w.dirty = true;
         return fail(c.status, "%s (code %d, detail %d)", status_text(c.status), c.status, c.info);

@@ -112,7 +112,7 @@ struct Traits {
     static constexpr int VW = KeyOps<K>::VW;
     static constexpr int VPT = VPT_;
     static constexpr int E = VPT_ * KeyOps<K_>::VW;  // keys per thread per tile
-    static constexpr int T = kThreads * E;
+    static constexpr int T = kDThreads * E;  // keys per partition tile
     static constexpr int LEAF = LEAF_;
     static constexpr int SMALL = SMALL_;
     static_assert(E <= 32, "per-thread flags are kept in one 32-bit mask");
@@ -159,6 +159,15 @@ __device__ __forceinline__ long long ld_relaxed_s64(const long long *p)
     long long v;
     asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+// Fetch-and-add with release (this thread's earlier writes, and the writes it
+// has observed through a CTA barrier, become visible first) and acquire (the
+// writes released by earlier adders become visible to this thread).
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long *p, unsigned long long v)
+{
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
 }
 __device__ __forceinline__ uint64_t global_ns()
 {

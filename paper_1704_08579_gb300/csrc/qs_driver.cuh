@@ -178,13 +178,13 @@ struct DriverSmem {
     alignas(128) typename Tr::K kbuf[2][Tr::T];
     alignas(128) typename Tr::V vbuf[2][Tr::KV ? Tr::T : 4];
     alignas(8) unsigned long long bar[2];
-    int wcount[Tr::VPT * kWarps];
+    int wcount[Tr::VPT * kDWarps];
     long long excl;
     long long first;
     int low_total;
     int eq_total;
     int next_low;  // early count of the prefetched tile (warps 1..7)
-    long long tm[8];  // per-phase cycles (thread 0, profiling on)
+    long long tm[kProfSlots];  // per-phase cycles and counters (profiling on)
     int last;
     int abort;
     WorkItem w[2];  // [0] current, [1] next
@@ -193,6 +193,11 @@ struct DriverSmem {
     int nt_ok[2];
     int64_t c_off[2], c_len[2];
     int c_kind[2];  // 0 none, 1 finished (equal keys), 2 leaf, 3 partition (sampled pivot), 4 partition ('<=', same pivot)
+    WorkItem wp;    // written tile whose release is deferred
+    WorkItem wf;    // task to complete (its last tile was just released)
+    int has_prev;   // wp is pending
+    int prev_eq;    // pivot-equal keys counted in wp's tile
+    int prev_last;  // the release of wp completed its task
 };
 
 template <class Tr>
@@ -286,19 +291,23 @@ __device__ WorkItem resolve_blocking(const Args<typename Tr::K, typename Tr::V> 
 // ---------------------------------------------------------------------------
 // Decoupled look-back by warp 0 (Merrill & Garland).  Returns the number of
 // lower-side keys in all preceding tiles of the task, or -1 if the wait ran
-// out or another CTA reported an error.
+// out or another CTA reported an error.  Lane l of a window looks at tile
+// idx - l; the walk stops at the nearest inclusive prefix behind a run of
+// published aggregates.  nwin / nspin count the windows read and the re-reads
+// of unpublished words (profiling).
 // ---------------------------------------------------------------------------
 static __device__ long long lookback(unsigned long long *words, int tile, unsigned long long low, Ctrl *c,
-                                     uint64_t limit_ns, bool published)
+                                     uint64_t limit_ns, bool published, int &nwin, int &nspin)
 {
     const int lane = threadIdx.x & 31;
+    nwin = nspin = 0;
     if (tile == 0) {
         if (lane == 0 && !published) st_relaxed_u64(words, kFlagPrefix | low);
         return 0;
     }
     if (lane == 0 && !published) st_relaxed_u64(words + tile, kFlagAggregate | low);
     long long excl = 0;
-    int idx = tile - 1;  // lane l looks at tile idx - l
+    int idx = tile - 1;
     uint64_t t0 = 0;
     int spins = 0;
     unsigned long long s = idx - lane >= 0 ? ld_relaxed_u64(words + (idx - lane)) : kFlagPrefix;
@@ -315,6 +324,7 @@ static __device__ long long lookback(unsigned long long *words, int tile, unsign
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             excl += v;
+            ++nwin;
             if (first_p < first_nr) break;  // reached an inclusive prefix
             idx -= 32;
             const int j = idx - lane;
@@ -323,6 +333,7 @@ static __device__ long long lookback(unsigned long long *words, int tile, unsign
         }
         // A tile before the nearest prefix has not published yet: re-read it.
         if (flag == 0) s = ld_relaxed_u64(words + (idx - lane));
+        ++nspin;
         if (++spins == 64) {
             spins = 0;
             int bad = 0;
@@ -367,7 +378,7 @@ __device__ __forceinline__ int count_low(const typename Tr::K *buf, typename Key
     constexpr int NV = Tr::T / Tr::VW;
     const Vec *v = reinterpret_cast<const Vec *>(buf);
     int cnt = 0;
-    for (int i = threadIdx.x - 32; i < NV; i += kThreads - 32) {
+    for (int i = threadIdx.x - 32; i < NV; i += kDThreads - 32) {
         typename Tr::K tmp[Tr::VW];
         Ops::split(v[i], tmp);
 #pragma unroll
@@ -402,14 +413,39 @@ __device__ __forceinline__ int count_low_any(const typename Tr::K *buf, uint64_t
 }
 
 // ---------------------------------------------------------------------------
+// Release of a written tile (one thread, after a CTA barrier that follows the
+// tile's stores): its pivot-equal count, a fence, then the task's tile
+// counter.  The tile that arrives last completes the task, so no CTA ever
+// waits for the others.  The release is deferred into the next tile (see
+// partition_tile), where the fence finds the stores already drained.
+// ---------------------------------------------------------------------------
+template <class Tr>
+__device__ __forceinline__ void release_prev(const Args<typename Tr::K, typename Tr::V> &a, DriverSmem<Tr> &sm)
+{
+    int last = 0;
+    if (sm.has_prev) {
+        Task *t = a.tasks + sm.wp.task;
+        if (sm.prev_eq) atomicAdd(&t->eq, static_cast<unsigned long long>(sm.prev_eq));
+        // acq_rel: releases the tile's stores (and lt_total, eq); the last
+        // adder acquires every other tile's.
+        const unsigned long long done = atom_add_acq_rel_u64(&t->tiles_done, 1ull);
+        last = done == static_cast<unsigned long long>(sm.wp.ntiles - 1) ? 1 : 0;
+        if (last) sm.wf = sm.wp;
+        sm.has_prev = 0;
+    }
+    sm.prev_last = last;
+}
+
+// ---------------------------------------------------------------------------
 // One partition tile.  Vector k of thread t covers tile positions
 // k*NT*VW + t*VW + j, so the input order is (k, warp, lane, j).  The pivot
 // compare (the paper's vector compare into a mask) becomes warp ballots whose
 // popcounts give every key its rank among the tile's lower-side keys; a CTA
 // scan of the (k, warp) counts plus the look-back give its global position.
 // Keys are staged in shared memory in output order and written with
-// coalesced stores.  Returns 1 if this CTA completes the task, 0 if not, -1
-// on abort.
+// coalesced stores.  Returns 0, or -1 on abort.  On return sm.prev_last says
+// whether the deferred release of the previous tile completed its task
+// (sm.wf), which the caller then completes.
 // ---------------------------------------------------------------------------
 template <class Tr>
 __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, const WorkItem &w, WorkItem &nx,
@@ -420,7 +456,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     using Ops = KeyOps<K>;
     using Vec = typename Ops::Vec;
     constexpr int VW = Tr::VW, VPT = Tr::VPT, T = Tr::T, E = Tr::E;
-    constexpr int NC = VPT * kWarps;       // (vector, warp) chunk counts
+    constexpr int NC = VPT * kDWarps;       // (vector, warp) chunk counts
     constexpr int CPL = (NC + 31) / 32;    // chunk counts per lane in the scan
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -447,11 +483,11 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
             K tmp[VW];
-            Ops::split(sv[k * kThreads + tid], tmp);
+            Ops::split(sv[k * kDThreads + tid], tmp);
 #pragma unroll
             for (int j = 0; j < VW; ++j) key[k * VW + j] = tmp[j];
             if constexpr (Tr::KV) {
-                const int4 vv = reinterpret_cast<const int4 *>(sm.vbuf[b])[k * kThreads + tid];
+                const int4 vv = reinterpret_cast<const int4 *>(sm.vbuf[b])[k * kDThreads + tid];
                 val[k * VW + 0] = vv.x;
                 val[k * VW + 1] = vv.y;
                 val[k * VW + 2] = vv.z;
@@ -464,7 +500,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         const V *__restrict__ svv = a.vals[w.src];
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
-            const int64_t e = base + static_cast<int64_t>(k) * kThreads * VW + tid * VW;
+            const int64_t e = base + static_cast<int64_t>(k) * kDThreads * VW + tid * VW;
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
                 const int64_t p = e + j;
@@ -490,7 +526,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
             pre += __popc(bb & lt_mask);
         }
         rank[k] = pre;
-        if (lane == 0) sm.wcount[k * kWarps + warp] = tot;
+        if (lane == 0) sm.wcount[k * kDWarps + warp] = tot;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) eq += __shfl_xor_sync(0xffffffffu, eq, o);
@@ -498,7 +534,35 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     __syncthreads();
     QS_TICK(2);
 
-    // Warp 0: exclusive scan of the chunk counts, then the look-back.
+    // Staging in output order (lower-side keys at [0, L), upper-side keys
+    // after them) depends only on this tile's own counts, not on the global
+    // offset; so warp 0 scans the chunk counts and releases the other warps
+    // (named barrier 2) before it starts the look-back, and they stage their
+    // keys meanwhile.
+    const int64_t vstart = base > off ? base : off;
+    const int64_t vend = base + T < end ? base + T : end;
+    const int nvalid = static_cast<int>(vend - vstart);
+    const int vofs = static_cast<int>(vstart - base);  // window slots before the first valid key
+    K *stage_k = sm.kbuf[b];
+    V *stage_v = sm.vbuf[b];
+    auto stage = [&](int L) {
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            int r = sm.wcount[k * kDWarps + warp] + rank[k];
+            const int e = k * kDThreads * VW + tid * VW - vofs;
+#pragma unroll
+            for (int j = 0; j < VW; ++j) {
+                const int i = k * VW + j;
+                const bool lo = (lowm >> i) & 1u;
+                if ((validm >> i) & 1u) {
+                    const int s = lo ? r : L + (e + j - r);
+                    stage_k[s] = key[i];
+                    if constexpr (Tr::KV) stage_v[s] = val[i];
+                }
+                r += lo ? 1 : 0;
+            }
+        }
+    };
     if (warp == 0) {
         int v[CPL];
         int sum = 0;
@@ -522,64 +586,60 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
             if (idx < NC) sm.wcount[idx] = run;
             run += v[i];
         }
+        if (lane == 0) sm.low_total = total;
+        __syncwarp();
+        asm volatile("bar.arrive 2, %0;" ::"n"(kDThreads) : "memory");
+        const long long tlb = a.profile ? clock64() : 0;
+        int nwin, nspin;
         const long long excl = lookback(a.pool + w.pool, w.tile, static_cast<unsigned long long>(total), a.ctrl,
-                                        a.wait_limit_ns, w.a_pub != 0);
+                                        a.wait_limit_ns, w.a_pub != 0, nwin, nspin);
+        if (a.profile && lane == 0) {
+            sm.tm[8] += clock64() - tlb;
+            sm.tm[10] += nwin;
+            sm.tm[11] += nspin;
+        }
         if (lane == 0) {
             sm.excl = excl;
-            sm.low_total = total;
             sm.abort = excl < 0;
             if (excl >= 0 && w.tile == w.ntiles - 1)
                 st_relaxed_u64(&a.tasks[w.task].lt_total, static_cast<unsigned long long>(excl + total));
         }
-    } else if (nx.kind == 1 && nx.full && !nx.a_pub) {
-        // Meanwhile warps 1..7 count the prefetched next tile and publish its
-        // aggregate at once, so tiles after it never wait for this CTA to
-        // finish the current tile.
-        if (mbar_wait_bounded(&sm.bar[b ^ 1], (phases >> (b ^ 1)) & 1u, a.ctrl, a.wait_limit_ns)) {
-            int cnt = count_low_any<Tr>(sm.kbuf[b ^ 1], nx.pivot, nx.mode);
+        stage(total);
+    } else {
+        if (nx.kind == 1 && nx.full && !nx.a_pub) {
+            // Warps 1..7 first count the prefetched next tile and publish its
+            // aggregate, so tiles after it never wait for this CTA to finish
+            // the current tile.
+            const long long tmb = (a.profile && tid == 32) ? clock64() : 0;
+            const bool landed = mbar_wait_bounded(&sm.bar[b ^ 1], (phases >> (b ^ 1)) & 1u, a.ctrl, a.wait_limit_ns);
+            if (a.profile && tid == 32) sm.tm[9] += clock64() - tmb;
+            if (landed) {
+                int cnt = count_low_any<Tr>(sm.kbuf[b ^ 1], nx.pivot, nx.mode);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            if (lane == 0) atomicAdd(&sm.next_low, cnt);
+                for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                if (lane == 0) atomicAdd(&sm.next_low, cnt);
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(kDThreads - 32) : "memory");
+            if (tid == 32) {
+                const unsigned long long c = static_cast<unsigned long long>(sm.next_low);
+                st_relaxed_u64(a.pool + nx.pool + nx.tile, (nx.tile == 0 ? kFlagPrefix : kFlagAggregate) | c);
+                sm.next_low = 0;
+                nx.a_pub = 1;
+            }
         }
-        asm volatile("bar.sync 1, %0;" ::"n"(kThreads - 32) : "memory");
         if (tid == 32) {
-            const unsigned long long c = static_cast<unsigned long long>(sm.next_low);
-            st_relaxed_u64(a.pool + nx.pool + nx.tile, (nx.tile == 0 ? kFlagPrefix : kFlagAggregate) | c);
-            sm.next_low = 0;
-            nx.a_pub = 1;
+            const long long trl = a.profile ? clock64() : 0;
+            release_prev<Tr>(a, sm);
+            if (a.profile) sm.tm[5] += clock64() - trl;
         }
+        asm volatile("bar.sync 2, %0;" ::"n"(kDThreads) : "memory");  // chunk offsets are ready
+        stage(sm.low_total);
     }
     __syncthreads();
     QS_TICK(3);
     if (sm.abort) return -1;
-
     const int L = sm.low_total;
     const long long excl = sm.excl;
-    const int64_t vstart = base > off ? base : off;
-    const int64_t vend = base + T < end ? base + T : end;
-    const int nvalid = static_cast<int>(vend - vstart);
-    const int vofs = static_cast<int>(vstart - base);  // window slots before the first valid key
-    K *stage_k = sm.kbuf[b];
-    V *stage_v = sm.vbuf[b];
-
-    // Stage in output order: lower-side keys at [0, L), upper-side keys after.
-#pragma unroll
-    for (int k = 0; k < VPT; ++k) {
-        int r = sm.wcount[k * kWarps + warp] + rank[k];
-        const int e = k * kThreads * VW + tid * VW - vofs;
-#pragma unroll
-        for (int j = 0; j < VW; ++j) {
-            const int i = k * VW + j;
-            const bool lo = (lowm >> i) & 1u;
-            if ((validm >> i) & 1u) {
-                const int s = lo ? r : L + (e + j - r);
-                stage_k[s] = key[i];
-                if constexpr (Tr::KV) stage_v[s] = val[i];
-            }
-            r += lo ? 1 : 0;
-        }
-    }
-    __syncthreads();
 
     // Lower side: [off + excl, +L); upper side (reverse order) ends at
     // end - 1 - hpre, where hpre = upper-side keys of the earlier tiles.
@@ -590,7 +650,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         K *__restrict__ hi_k = a.keys[w.src ^ 1] + (end - 1 - hpre + L);  // key s >= L goes to hi_k - s
         V *__restrict__ lo_v = a.vals[w.src ^ 1] + (off + excl);
         V *__restrict__ hi_v = a.vals[w.src ^ 1] + (end - 1 - hpre + L);
-        for (int s = tid; s < nvalid; s += kThreads) {
+        for (int s = tid; s < nvalid; s += kDThreads) {
             const bool lo = s < L;
             *(lo ? lo_k + s : hi_k - s) = stage_k[s];
             if constexpr (Tr::KV) *(lo ? lo_v + s : hi_v - s) = stage_v[s];
@@ -600,40 +660,16 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     }
     __syncthreads();
     QS_TICK(4);
-    if (tid == 0) {
-        Task *t = a.tasks + w.task;
-        if (sm.eq_total) atomicAdd(&t->eq, static_cast<unsigned long long>(sm.eq_total));
+    if (tid == 0) {  // this tile's release is deferred into the next tile
+        sm.wp = w;
+        sm.prev_eq = sm.eq_total;
         sm.eq_total = 0;
-        __threadfence();  // release this tile's stores
-        int last = 0;
-        if (w.tile != w.ntiles - 1) {
-            atomicAdd(&t->tiles_done, 1ull);
-        } else {
-            // The last tile completes the task once every other tile has released.
-            last = 1;
-            const unsigned long long want = static_cast<unsigned long long>(w.ntiles - 1);
-            if (ld_acquire_u64(&t->tiles_done) != want) {
-                const uint64_t t0 = global_ns();
-                unsigned ns = 32;
-                while (ld_acquire_u64(&t->tiles_done) != want) {
-                    if (global_ns() - t0 > a.wait_limit_ns || ld_relaxed_s32(&a.ctrl->status) != 0) {
-                        set_error(a.ctrl, kErrTimeout, 5);
-                        last = -1;
-                        break;
-                    }
-                    __nanosleep(ns);
-                    ns = ns < 512 ? ns * 2 : ns;
-                }
-            }
-            __threadfence();
-        }
-        sm.last = last;
+        sm.has_prev = 1;
     }
     __syncthreads();
-    QS_TICK(5);
 #undef QS_TICK
     if (a.profile && tid == 0) sm.tm[7] += 1;
-    return sm.last;
+    return 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -717,7 +753,7 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
     }
     __syncthreads();
     for (int i = 0; i < 2; ++i)
-        if (sm.nt_ok[i]) publish_task(a.owner, sm.nt[i]);
+        if (sm.nt_ok[i]) publish_task(a.owner, sm.nt[i], -1, kDThreads);
     for (int i = 0; i < 2; ++i) {
         // Finished run of equal keys: copy back only if it sits in scratch.
         if (sm.c_kind[i] != 1 || dst != 1) continue;
@@ -732,7 +768,7 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
         __syncthreads();
         const long long first = sm.first;
         if (first >= 0) {
-            for (int64_t q = tid; q < chunks; q += kThreads) {
+            for (int64_t q = tid; q < chunks; q += kDThreads) {
                 Leaf l;
                 l.off = coff + q * kCopyChunk;
                 const int64_t rem = clen - q * kCopyChunk;
@@ -751,11 +787,26 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
     __syncthreads();
 }
 
+// Releases the deferred tile now (whole CTA) and completes its task if it was
+// the last one.
+template <class Tr>
+__device__ void flush_release(const Args<typename Tr::K, typename Tr::V> &a, DriverSmem<Tr> &sm)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const long long trl = a.profile ? clock64() : 0;
+        release_prev<Tr>(a, sm);
+        if (a.profile) sm.tm[5] += clock64() - trl;
+    }
+    __syncthreads();
+    if (sm.prev_last) finish_task<Tr>(a, sm.wf, sm);
+}
+
 // ---------------------------------------------------------------------------
 // Persistent partition kernel.
 // ---------------------------------------------------------------------------
 template <class Tr, int MinBlocks>
-__global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typename Tr::K, typename Tr::V> a)
+__global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typename Tr::K, typename Tr::V> a)
 {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     DriverSmem<Tr> &sm = *reinterpret_cast<DriverSmem<Tr> *>(dyn_smem);
@@ -764,12 +815,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
     uint32_t pending = 0;  // bit b: a bulk load into buffer b is issued and not yet consumed
     long long t_wait = a.profile ? clock64() : 0;
     if (tid == 0) {
-        for (int i = 0; i < 8; ++i) sm.tm[i] = 0;
+        for (int i = 0; i < kProfSlots; ++i) sm.tm[i] = 0;
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
         fence_mbar_init();
         sm.eq_total = 0;
         sm.next_low = 0;
+        sm.has_prev = 0;
+        sm.prev_last = 0;
         WorkItem none;
         none.kind = 0;
         const long long g = static_cast<long long>(atomicAdd(&a.ctrl->ticket_head, 1ull));
@@ -785,10 +838,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
     while (sm.w[0].kind == 1) {
         if (tid == 0) {
             // Claim the next ticket now; prefetch its tile if its task is known.
+            const long long th = a.profile ? clock64() : 0;
             const long long g = static_cast<long long>(atomicAdd(&a.ctrl->ticket_head, 1ull));
             sm.next_ticket = g;
             sm.w[1] = try_resolve<Tr>(a, g, sm.w[0]);
             if (sm.w[1].kind == 1) issue_tile_load<Tr>(a, sm.w[1], sm, b ^ 1);
+            if (a.profile) sm.tm[13] += clock64() - th;
         }
         const int r = partition_tile<Tr>(a, sm.w[0], sm.w[1], sm, b, phases);
         pending &= ~(1u << b);
@@ -797,12 +852,15 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
             aborted = true;
             break;
         }
-        if (r == 1) {
+        if (sm.prev_last) {
             const long long t6 = a.profile ? clock64() : 0;
-            finish_task<Tr>(a, sm.w[0], sm);
+            finish_task<Tr>(a, sm.wf, sm);
             if (a.profile && tid == 0) sm.tm[6] += clock64() - t6;
         }
         if (sm.w[1].kind == 0) {
+            // About to wait for work: release the last written tile first, as
+            // the work waited for may be its task's children.
+            flush_release<Tr>(a, sm);
             const long long t0w = a.profile ? clock64() : 0;
             __syncthreads();
             if (tid == 0) {
@@ -818,19 +876,20 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) driver_kernel(Args<typena
         __syncthreads();
         b ^= 1;
     }
+    if (!aborted) flush_release<Tr>(a, sm);
     // Never leave while a bulk copy may still be writing this CTA's shared memory.
     for (int i = 0; i < 2; ++i)
         if ((pending >> i) & 1u) mbar_wait_bounded(&sm.bar[i], (phases >> i) & 1u, a.ctrl, a.wait_limit_ns);
     __syncthreads();
     if (a.profile && tid == 0)
-        for (int i = 0; i < 8; ++i) atomicAdd(&a.ctrl->cycles[i], static_cast<unsigned long long>(sm.tm[i]));
+        for (int i = 0; i < kProfSlots; ++i) atomicAdd(&a.ctrl->cycles[i], static_cast<unsigned long long>(sm.tm[i]));
     if (aborted) return;
     // Clean exit: every task is finished, so no CTA reads the look-back words
     // or the ticket owners any more; clear this CTA's share for the next call.
     if (ld_relaxed_s32(&a.ctrl->status) == 0) {
         const unsigned long long used = ld_relaxed_u64(&a.ctrl->pool_cursor);
-        const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * kThreads;
-        for (unsigned long long i = blockIdx.x * kThreads + tid; i < used; i += stride) {
+        const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * kDThreads;
+        for (unsigned long long i = blockIdx.x * kDThreads + tid; i < used; i += stride) {
             a.pool[i] = 0;
             a.owner[i] = 0;
         }
@@ -860,7 +919,7 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(Args<typename Tr::K, ty
         c->part_tasks = c->part_keys = c->leaf_parts = c->leaf_keys = c->copy_keys = c->max_depth = 0;
         c->lt_result = 0;
         c->exited = 0;
-        for (int i = 0; i < 8; ++i) c->cycles[i] = 0;
+        for (int i = 0; i < kProfSlots; ++i) c->cycles[i] = 0;
         ok = 0;
         __threadfence();
     }

@@ -28,6 +28,8 @@ namespace qs {
 
 constexpr int kThreads = 256;            // threads per CTA in every kernel
 constexpr int kWarps = kThreads / 32;
+constexpr int kDThreads = 256;           // threads per CTA of the persistent partition kernel
+constexpr int kDWarps = kDThreads / 32;
 
 constexpr uint64_t kFlagAggregate = 1ull << 62;
 constexpr uint64_t kFlagPrefix = 2ull << 62;
@@ -62,6 +64,8 @@ struct alignas(16) Leaf {
 constexpr int kLeafScratch = 1;
 constexpr int kLeafFinal = 2;
 
+constexpr int kProfSlots = 16;  // driver profiling slots (qs_stats.driver_cycles)
+
 struct alignas(128) Ctrl {
     unsigned long long ticket_head;  // next ticket to hand out
     unsigned long long n_tasks, pool_cursor;
@@ -73,7 +77,7 @@ struct alignas(128) Ctrl {
     unsigned long long part_tasks, part_keys, leaf_parts, leaf_keys, copy_keys, max_depth;
     unsigned long long lt_result;  // split index of a partition-only call
     unsigned long long exited;     // CTAs of the persistent kernel that left cleanly
-    unsigned long long cycles[8];  // per-phase SM cycles (profiling on)
+    unsigned long long cycles[kProfSlots];  // per-phase SM cycles and counters (profiling on)
 };
 
 // Arguments of the device kernels (passed by value).

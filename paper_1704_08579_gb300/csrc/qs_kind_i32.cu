@@ -5,7 +5,7 @@ namespace qs {
 
 namespace {
 using Tr = Traits<int32_t, false, 4, 8192, 512>;
-using L = Launcher<Tr, 3, 2>;
+using L = Launcher<Tr, 3 * 256 / kDThreads, 2>;  // driver CTAs per SM: register-bound at 80 per thread
 }  // namespace
 
 int launch_i32(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg) { return L::launch(a, cfg); }

@@ -5,7 +5,7 @@ namespace qs {
 
 namespace {
 using Tr = Traits<int32_t, true, 4, 4096, 512>;
-using L = Launcher<Tr, 3, 2>;
+using L = Launcher<Tr, 3 * 256 / kDThreads, 2>;  // driver CTAs per SM: register-bound at 80 per thread
 }  // namespace
 
 int launch_kv(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg) { return L::launch(a, cfg); }

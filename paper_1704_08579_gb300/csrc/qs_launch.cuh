@@ -42,7 +42,7 @@ struct Launcher {
         int rc = prepare();
         if (rc) return rc;
         if (which == 0)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, driver_kernel<Tr, DriverMin>, kThreads,
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, driver_kernel<Tr, DriverMin>, kDThreads,
                                                                  kDriverSmem);
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, leaf_kernel<Tr, LeafMin>, kThreads, 0);
     }
@@ -60,7 +60,7 @@ struct Launcher {
         }
         if (cfg.profile) cudaEventRecord(ev[1], s);
         if (a.partition_only || a.seg_off || a.n > a.leaf_max)
-            driver_kernel<Tr, DriverMin><<<cfg.grid_driver, kThreads, kDriverSmem, s>>>(a);
+            driver_kernel<Tr, DriverMin><<<cfg.grid_driver, kDThreads, kDriverSmem, s>>>(a);
         if (cfg.profile) cudaEventRecord(ev[2], s);
         if (!a.partition_only) leaf_kernel<Tr, LeafMin><<<cfg.grid_leaf, kThreads, 0, s>>>(a);
         if (cfg.profile) cudaEventRecord(ev[3], s);
