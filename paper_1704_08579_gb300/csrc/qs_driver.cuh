@@ -173,6 +173,9 @@ struct WorkItem {
     uint64_t pivot;
 };
 
+// Warps 1 .. kDWarps-2 count the prefetched tile during the look-back.
+constexpr int kCountThreads = kDThreads - 64;
+
 template <class Tr>
 struct DriverSmem {
     alignas(128) typename Tr::K kbuf[2][Tr::T];
@@ -378,7 +381,7 @@ __device__ __forceinline__ int count_low(const typename Tr::K *buf, typename Key
     constexpr int NV = Tr::T / Tr::VW;
     const Vec *v = reinterpret_cast<const Vec *>(buf);
     int cnt = 0;
-    for (int i = threadIdx.x - 32; i < NV; i += kDThreads - 32) {
+    for (int i = threadIdx.x - 32; i < NV; i += kCountThreads) {
         typename Tr::K tmp[Tr::VW];
         Ops::split(v[i], tmp);
 #pragma unroll
@@ -605,11 +608,11 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
                 st_relaxed_u64(&a.tasks[w.task].lt_total, static_cast<unsigned long long>(excl + total));
         }
         stage(total);
-    } else {
+    } else if (warp < kDWarps - 1) {
         if (nx.kind == 1 && nx.full && !nx.a_pub) {
-            // Warps 1..7 first count the prefetched next tile and publish its
-            // aggregate, so tiles after it never wait for this CTA to finish
-            // the current tile.
+            // The middle warps first count the prefetched next tile and
+            // publish its aggregate, so tiles after it never wait for this CTA
+            // to finish the current tile.
             const long long tmb = (a.profile && tid == 32) ? clock64() : 0;
             const bool landed = mbar_wait_bounded(&sm.bar[b ^ 1], (phases >> (b ^ 1)) & 1u, a.ctrl, a.wait_limit_ns);
             if (a.profile && tid == 32) sm.tm[9] += clock64() - tmb;
@@ -619,7 +622,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
                 for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
                 if (lane == 0) atomicAdd(&sm.next_low, cnt);
             }
-            asm volatile("bar.sync 1, %0;" ::"n"(kDThreads - 32) : "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(kCountThreads) : "memory");
             if (tid == 32) {
                 const unsigned long long c = static_cast<unsigned long long>(sm.next_low);
                 st_relaxed_u64(a.pool + nx.pool + nx.tile, (nx.tile == 0 ? kFlagPrefix : kFlagAggregate) | c);
@@ -627,11 +630,17 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
                 nx.a_pub = 1;
             }
         }
-        if (tid == 32) {
+        asm volatile("bar.sync 2, %0;" ::"n"(kDThreads) : "memory");  // chunk offsets are ready
+        stage(sm.low_total);
+    } else {
+        // The last warp releases the previous tile meanwhile: its fence waits
+        // for this SM's earlier stores to drain, off the other warps' path.
+        if (lane == 0) {
             const long long trl = a.profile ? clock64() : 0;
             release_prev<Tr>(a, sm);
             if (a.profile) sm.tm[5] += clock64() - trl;
         }
+        __syncwarp();
         asm volatile("bar.sync 2, %0;" ::"n"(kDThreads) : "memory");  // chunk offsets are ready
         stage(sm.low_total);
     }
