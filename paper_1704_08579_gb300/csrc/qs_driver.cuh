@@ -234,6 +234,15 @@ __device__ WorkItem try_resolve(const Args<typename Tr::K, typename Tr::V> &a, l
     w.kind = 0;
     w.ticket = g;
     if (g >= a.pool_cap) return w;  // beyond every ticket that can be published
+    if (hint.kind == 1 && g >= hint.pool && g < hint.pool + hint.ntiles) {
+        // Another tile of the task in hand: tasks own contiguous ticket
+        // ranges, so no need to look the owner up.
+        w.tile = static_cast<int>(g - w.pool);
+        w.kind = 1;
+        w.a_pub = 0;
+        fill_tile<Tr>(a, w);
+        return w;
+    }
     const int id1 = ld_acquire_s32(a.owner + g);
     if (id1 <= 0 || id1 > a.task_cap) {
         if (id1 != 0) set_error(a.ctrl, kErrInternalIndex, 2);
