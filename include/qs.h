@@ -254,8 +254,11 @@ typedef struct {
      * [9] cycles warps 1..7 waited for the prefetched tile, [10] look-back
      * windows of 32 words read, [11] re-reads of unpublished words;
      * [13] claiming and resolving the next ticket and issuing its load
-     * (thread 0); [12], [14], [15] unused. */
-    int64_t driver_cycles[16];
+     * (thread 0); [12], [14], [15] look-back phase as seen by the counting
+     * warps, warp 0 and the last warp; [16] staging (warp 0), [17] staging
+     * (last warp), [18] the count phase's compare-and-ballot work (thread 0),
+     * [19..23] unused. */
+    int64_t driver_cycles[24];
     int64_t bucket_max;     /* learned / bucket pass: largest bucket */
     int64_t bucket_over;    /* learned / bucket pass: buckets above 4x their even share */
     int64_t bucket_dev;     /* learned / bucket pass: sum over the B buckets of |size * B - n|;

@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
         "n", "kind", "part_tasks", "part_keys", "leaf_parts", "leaf_keys", "copy_keys", "max_depth",
         "lookback_words", "grid_driver", "grid_leaf")] + [
         (name, ctypes.c_double) for name in ("ms_driver", "ms_leaf", "ms_copy", "ms_total")] + [
-        ("driver_cycles", ctypes.c_int64 * 16), ("bucket_max", ctypes.c_int64), ("bucket_over", ctypes.c_int64),
+        ("driver_cycles", ctypes.c_int64 * 24), ("bucket_max", ctypes.c_int64), ("bucket_over", ctypes.c_int64),
         ("bucket_dev", ctypes.c_int64)]
 
 

@@ -543,8 +543,10 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) eq += __shfl_xor_sync(0xffffffffu, eq, o);
     if (lane == 0 && eq) atomicAdd(&sm.eq_total, eq);
+    if (a.profile && tid == 0) sm.tm[18] += clock64() - tprev;  // own work, before the barrier
     __syncthreads();
     QS_TICK(2);
+    const long long tph = a.profile ? clock64() : 0;  // start of the look-back phase
 
     // Staging in output order (lower-side keys at [0, L), upper-side keys
     // after them) depends only on this tile's own counts, not on the global
@@ -616,7 +618,13 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
             if (excl >= 0 && w.tile == w.ntiles - 1)
                 st_relaxed_u64(&a.tasks[w.task].lt_total, static_cast<unsigned long long>(excl + total));
         }
+        const long long tst = a.profile ? clock64() : 0;
         stage(total);
+        if (a.profile && lane == 0) {
+            const long long now = clock64();
+            sm.tm[16] += now - tst;
+            sm.tm[14] += now - tph;
+        }
     } else if (warp < kDWarps - 1) {
         if (nx.kind == 1 && nx.full && !nx.a_pub) {
             // The middle warps first count the prefetched next tile and
@@ -641,6 +649,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         }
         asm volatile("bar.sync 2, %0;" ::"n"(kDThreads) : "memory");  // chunk offsets are ready
         stage(sm.low_total);
+        if (a.profile && tid == 32) sm.tm[12] += clock64() - tph;
     } else {
         // The last warp releases the previous tile meanwhile: its fence waits
         // for this SM's earlier stores to drain, off the other warps' path.
@@ -651,7 +660,13 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         }
         __syncwarp();
         asm volatile("bar.sync 2, %0;" ::"n"(kDThreads) : "memory");  // chunk offsets are ready
+        const long long tst = a.profile ? clock64() : 0;
         stage(sm.low_total);
+        if (a.profile && lane == 0) {
+            const long long now = clock64();
+            sm.tm[17] += now - tst;
+            sm.tm[15] += now - tph;
+        }
     }
     __syncthreads();
     QS_TICK(3);

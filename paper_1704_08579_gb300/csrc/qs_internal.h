@@ -64,7 +64,7 @@ struct alignas(16) Leaf {
 constexpr int kLeafScratch = 1;
 constexpr int kLeafFinal = 2;
 
-constexpr int kProfSlots = 16;  // driver profiling slots (qs_stats.driver_cycles)
+constexpr int kProfSlots = 24;  // driver profiling slots (qs_stats.driver_cycles)
 
 struct alignas(128) Ctrl {
     unsigned long long ticket_head;  // next ticket to hand out
