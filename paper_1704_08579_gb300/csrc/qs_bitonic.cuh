@@ -108,88 +108,6 @@ __device__ __forceinline__ void warp_bitonic_sort(S (&k)[E])
     }
 }
 
-// ---------------------------------------------------------------------------
-// CTA-wide network: NT threads x E registers = P elements.  Stages whose
-// partner lies in another warp run in shared memory, padded by one element
-// every 32 to keep the blocked write/read free of bank conflicts.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
-
-template <int E, class S>
-__device__ __forceinline__ void regs_to_smem(const S (&k)[E], S *sk)
-{
-    const int base = threadIdx.x * E;
-#pragma unroll
-    for (int r = 0; r < E; ++r) sk[pad32(base + r)] = k[r];
-}
-
-template <int E, class S>
-__device__ __forceinline__ void smem_to_regs(S (&k)[E], const S *sk)
-{
-    const int base = threadIdx.x * E;
-#pragma unroll
-    for (int r = 0; r < E; ++r) k[r] = sk[pad32(base + r)];
-}
-
-template <class S>
-__device__ __forceinline__ void smem_cx(S *sk, int lo, int hi)
-{
-    const int a = pad32(lo), b = pad32(hi);
-    S x = sk[a], y = sk[b];
-    cx(x, y);
-    sk[a] = x;
-    sk[b] = y;
-}
-
-// Flip stage of block size 2^(lh+1) over P elements in shared memory.
-template <int NT, int P, class S>
-__device__ __forceinline__ void smem_flip(S *sk, int lh)
-{
-    const int half = 1 << lh;
-#pragma unroll 4
-    for (int c = threadIdx.x; c < P / 2; c += NT) {
-        const int blk = c >> lh, w = c & (half - 1);
-        const int b0 = blk << (lh + 1);
-        smem_cx(sk, b0 + w, b0 + 2 * half - 1 - w);
-    }
-}
-
-// Half-cleaner with partner distance 2^lj.
-template <int NT, int P, class S>
-__device__ __forceinline__ void smem_half(S *sk, int lj)
-{
-    const int j = 1 << lj;
-#pragma unroll 4
-    for (int c = threadIdx.x; c < P / 2; c += NT) {
-        const int lo = ((c >> lj) << (lj + 1)) + (c & (j - 1));
-        smem_cx(sk, lo, lo + j);
-    }
-}
-
-// Sorts NT*E elements held by the CTA (blocked layout); sk holds at least
-// pad32(NT*E) elements.
-template <int NT, int E, class S>
-__device__ __forceinline__ void cta_bitonic_sort(S (&k)[E], S *sk)
-{
-    constexpr int P = NT * E;
-    const int lane = threadIdx.x & 31;
-    warp_bitonic_sort<E, S>(k);
-    for (int sz = 64 * E, lg = __ffs(64 * E) - 1; sz <= P; sz <<= 1, ++lg) {  // lg = log2(sz)
-        regs_to_smem<E, S>(k, sk);
-        __syncthreads();
-        smem_flip<NT, P, S>(sk, lg - 1);
-        __syncthreads();
-        for (int lj = lg - 2; (1 << lj) >= 32 * E; --lj) {
-            smem_half<NT, P, S>(sk, lj);
-            __syncthreads();
-        }
-        smem_to_regs<E, S>(k, sk);
-        __syncthreads();
-        for (int j = 16 * E; j >= E; j >>= 1) shfl_half<E, S>(k, j / E, (lane & (j / E)) != 0);
-        reg_half<E, E / 2>(k);
-    }
-}
-
 }  // namespace qs
 
 namespace qs {
@@ -207,8 +125,8 @@ namespace qs {
 // This is the direction-alternating form of Batcher's network (merge block
 // 2^m, stages on bits m-1 .. 0, descending where index bit m is set), which
 // needs single-bit stages only.  Padding with the largest key still ends up
-// at the tail: it is the largest value, and pads that tie with real keys are
-// bit-identical words.
+// at the tail: the last merge is ascending, the pad is the largest value, and
+// pads that tie with real keys are bit-identical words.
 // ---------------------------------------------------------------------------
 // Shared-memory slot of element i: one pad word per 128 bytes keeps every
 // layout's accesses free of bank conflicts (PSH = 4 for 8-byte keys, 5 for
@@ -259,115 +177,71 @@ __device__ __forceinline__ void group_sync(int bar, int nthreads)
         asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nthreads) : "memory");
 }
 
-// Ordered pair: (min, max) ascending, (max, min) descending.
-template <bool DESC, class S>
-__device__ __forceinline__ void cx_dir(S &a, S &b)
-{
-    if constexpr (sizeof(S) == 4) {
-        const S lo = min(a, b), hi = max(a, b);
-        a = DESC ? hi : lo;
-        b = DESC ? lo : hi;
-    } else {
-        const bool sw = DESC ? (a < b) : (b < a);
-        const S x = sw ? b : a;
-        b = sw ? a : b;
-        a = x;
-    }
-}
-
-// One stage on register bit RB with the same direction for the whole thread.
-template <int E, int RB, bool DESC, class S>
-__device__ __forceinline__ void reg_stage_u(S (&k)[E])
+// One stage on register bit RB, every comparator ascending.
+template <int E, int RB, class S>
+__device__ __forceinline__ void reg_stage_asc(S (&k)[E])
 {
 #pragma unroll
     for (int r = 0; r < E; ++r)
-        if (!(r & (1 << RB))) cx_dir<DESC, S>(k[r], k[r | (1 << RB)]);
+        if (!(r & (1 << RB))) cx(k[r], k[r | (1 << RB)]);
 }
 
-// One stage on register bit RB whose direction is register bit MRB.
-template <int E, int RB, int MRB, class S>
-__device__ __forceinline__ void reg_stage_p(S (&k)[E])
+// The stages d = D, D-1, ..., 0 of merge m that exist (d < m), each in the
+// layout that holds bit d: c(d) = LE*floor(d/LE), clamped to L-LE.  `cur` is
+// the group's current layout.
+template <int E, int LE, int L, int D, class S>
+__device__ __forceinline__ void merge_stages(S (&k)[E], S *sm, int g, int m, int &cur, int bar, int nthreads)
 {
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        if (r & (1 << RB)) continue;
-        if ((r >> MRB) & 1)
-            cx_dir<true, S>(k[r], k[r | (1 << RB)]);
-        else
-            cx_dir<false, S>(k[r], k[r | (1 << RB)]);
+    if constexpr (D >= 0) {
+        constexpr int C = (D / LE) * LE > L - LE ? L - LE : (D / LE) * LE;
+        if (D < m) {
+            if (cur != C) {
+                group_sync(bar, nthreads);
+                lay_store<E, LE, S>(k, sm, g, cur);
+                group_sync(bar, nthreads);
+                lay_load<E, LE, S>(k, sm, g, C);
+                cur = C;
+            }
+            reg_stage_asc<E, D - C, S>(k);
+        }
+        merge_stages<E, LE, L, D - 1, S>(k, sm, g, m, cur, bar, nthreads);
     }
 }
 
-template <int E, int RB, class S>
-__device__ __forceinline__ void reg_stage_rb(S (&k)[E], int mrb, bool tdesc)
-{
-    switch (mrb) {
-    case -1:
-        if (tdesc)
-            reg_stage_u<E, RB, true, S>(k);
-        else
-            reg_stage_u<E, RB, false, S>(k);
-        break;
-    case 1: if constexpr (RB < 1 && E > 2) reg_stage_p<E, RB, 1, S>(k); break;
-    case 2: if constexpr (RB < 2 && E > 4) reg_stage_p<E, RB, 2, S>(k); break;
-    case 3: if constexpr (RB < 3 && E > 8) reg_stage_p<E, RB, 3, S>(k); break;
-    case 4: if constexpr (RB < 4 && E > 16) reg_stage_p<E, RB, 4, S>(k); break;
-    default: break;
-    }
-}
-
-// A stage on register bit rb; mrb = register bit holding the direction, or -1
-// when the direction is the same for the whole thread (tdesc).
-template <int E, int LE, class S>
-__device__ __forceinline__ void reg_stage(S (&k)[E], int rb, int mrb, bool tdesc)
-{
-    static_assert(LE >= 1 && LE <= 5, "2..32 registers per thread");
-    switch (rb) {
-    case 0: reg_stage_rb<E, 0, S>(k, mrb, tdesc); break;
-    case 1: if constexpr (LE > 1) reg_stage_rb<E, 1, S>(k, mrb, tdesc); break;
-    case 2: if constexpr (LE > 2) reg_stage_rb<E, 2, S>(k, mrb, tdesc); break;
-    case 3: if constexpr (LE > 3) reg_stage_rb<E, 3, S>(k, mrb, tdesc); break;
-    default: if constexpr (LE > 4) reg_stage_rb<E, 4, S>(k, mrb, tdesc); break;
-    }
-}
-
-// Sorts the P = NG*E elements of a group.  On entry and exit the group holds
-// them in layout 0 (blocked: index = g*E + r); sm has room for pad32(P)
-// elements; g = thread index inside the group; L = log2(P).
-template <int E, int LE, class S>
-__device__ void group_bitonic_sort(S (&k)[E], S *sm, int g, int L, int bar, int nthreads)
+// Sorts the P = 2^L elements of a group of NG = P/E threads.  On entry and
+// exit the group holds them in layout 0 (blocked: index = g*E + r); sm has
+// room for padk(P) elements; g = thread index inside the group.
+//
+// Batcher's network merges blocks of 2^m elements for m = 1..L, the merge of
+// a block descending where index bit m is set.  Instead of comparators of
+// both directions, the elements of a descending block are complemented
+// (~x reverses the integer order) for the length of its merge, so every
+// comparator is the ascending (min, max) of the paper's network; between
+// merges m-1 and m an element flips when its index bits m-1 and m differ.
+// Merges 1..LE run inside each thread's registers (the flip form above,
+// block direction = index bit LE = thread bit 0).
+template <int E, int LE, int L, class S>
+__device__ void group_bitonic_sort(S (&k)[E], S *sm, int g, int bar, int nthreads)
 {
     // Every layout used has c == 0 or c >= LE, so LE >= PSH keeps lay_addr's
     // padding linear in the register index.
     static_assert(LE >= (sizeof(S) == 8 ? 4 : 5), "too few registers per thread for the padded layouts");
-    int cur = 0;
-    for (int m = 1; m <= L; ++m) {
-        for (int d = m - 1; d >= 0; --d) {
-            int c = (d / LE) * LE;
-            if (c > L - LE) c = L - LE;
-            if (c != cur) {
-                group_sync(bar, nthreads);
-                lay_store<E, LE, S>(k, sm, g, cur);
-                group_sync(bar, nthreads);
-                lay_load<E, LE, S>(k, sm, g, c);
-                cur = c;
-            }
-            int mrb = -1;
-            bool tdesc = false;  // the last merge (m == L) is ascending everywhere
-            if (m < L) {
-                if (m >= c && m < c + LE)
-                    mrb = m - c;
-                else
-                    tdesc = ((m < c ? (g >> m) : (g >> (m - LE))) & 1) != 0;
-            }
-            reg_stage<E, LE, S>(k, d - c, mrb, tdesc);
-        }
+    static_assert((1 << LE) == E && L >= LE + 5, "a group is at least one warp");
+    const S ones = ~S(0);
+    {
+        const S f = (g & 1) ? ones : S(0);
+#pragma unroll
+        for (int r = 0; r < E; ++r) k[r] ^= f;
+        reg_merges<E, 2, S>(k);
     }
-    if (cur != 0) {
-        group_sync(bar, nthreads);
-        lay_store<E, LE, S>(k, sm, g, cur);
-        group_sync(bar, nthreads);
-        lay_load<E, LE, S>(k, sm, g, 0);
+    int cur = 0;
+    for (int m = LE + 1; m <= L; ++m) {
+        const int before = (g >> (m - 1 - LE)) & 1;
+        const int during = m < L ? (g >> (m - LE)) & 1 : 0;
+        const S f = (before ^ during) ? ones : S(0);
+#pragma unroll
+        for (int r = 0; r < E; ++r) k[r] ^= f;
+        merge_stages<E, LE, L, L - 1, S>(k, sm, g, m, cur, bar, nthreads);
     }
 }
 

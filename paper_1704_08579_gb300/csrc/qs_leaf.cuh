@@ -106,7 +106,12 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     group_sync(bar, nthreads);
     S k[E];
     lay_load<E, LE, S>(k, gs, g, 0);
-    group_bitonic_sort<E, LE, S>(k, gs, g, L, bar, nthreads);
+    switch (L - LE) {  // log2 of the group's threads: 32 .. kThreads
+    case 5: group_bitonic_sort<E, LE, LE + 5, S>(k, gs, g, bar, nthreads); break;
+    case 6: group_bitonic_sort<E, LE, LE + 6, S>(k, gs, g, bar, nthreads); break;
+    case 7: group_bitonic_sort<E, LE, LE + 7, S>(k, gs, g, bar, nthreads); break;
+    default: group_bitonic_sort<E, LE, LE + 8, S>(k, gs, g, bar, nthreads); break;
+    }
     group_sync(bar, nthreads);
     lay_store<E, LE, S>(k, gs, g, 0);
     group_sync(bar, nthreads);

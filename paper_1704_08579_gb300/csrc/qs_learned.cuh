@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) sketch_kernel(const K *__restrict__ keys,
     if (t < NG) {
         S k[E];
         lay_load<E, LE, S>(k, sm, t, 0);
-        group_bitonic_sort<E, LE, S>(k, sm, t, 10, 1, NG);
+        group_bitonic_sort<E, LE, 10, S>(k, sm, t, 1, NG);
         group_sync(1, NG);
         lay_store<E, LE, S>(k, sm, t, 0);
     }
