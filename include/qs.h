@@ -256,8 +256,10 @@ typedef struct {
      * [13] claiming and resolving the next ticket and issuing its load
      * (thread 0); [12], [14], [15] look-back phase as seen by the counting
      * warps, warp 0 and the last warp; [16] staging (warp 0), [17] staging
-     * (last warp), [18] the count phase's compare-and-ballot work (thread 0),
-     * [19..23] unused. */
+     * (last warp), [18] the count phase's compare-and-ballot work (thread 0);
+     * leaf kernel: [19] packing parts into thread groups (thread 0), per
+     * group [20] loading, [21] the network, [23] storing, and [22] padding
+     * slots sorted. */
     int64_t driver_cycles[24];
     int64_t bucket_max;     /* learned / bucket pass: largest bucket */
     int64_t bucket_over;    /* learned / bucket pass: buckets above 4x their even share */

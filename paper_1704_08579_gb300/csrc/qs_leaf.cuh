@@ -101,23 +101,50 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     const typename Tr::K *gk = a.keys[src] + l.off;
     const typename Tr::V *gv = a.vals[src] + l.off;
     const int len = l.len;
-    // Coalesced load, tail padded with the largest key.
-    for (int i = g; i < P; i += nthreads) gs[padk<S>(i)] = i < len ? LK::load(gk, gv, i) : LK::largest();
+    long long t0 = (a.profile && g == 0) ? clock64() : 0;
+    // Coalesced load, tail padded with the largest key: all E loads of a
+    // thread are issued before the first one is used.
+    {
+        S t[E];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int i = g + r * nthreads;
+            t[r] = i < len ? LK::load(gk, gv, i) : LK::largest();
+        }
+#pragma unroll
+        for (int r = 0; r < E; ++r) gs[padk<S>(g + r * nthreads)] = t[r];
+    }
     group_sync(bar, nthreads);
     S k[E];
     lay_load<E, LE, S>(k, gs, g, 0);
+    if (a.profile && g == 0) {
+        const long long t = clock64();
+        atomicAdd(&a.ctrl->cycles[20], static_cast<unsigned long long>(t - t0));
+        t0 = t;
+    }
     switch (L - LE) {  // log2 of the group's threads: 32 .. kThreads
     case 5: group_bitonic_sort<E, LE, LE + 5, S>(k, gs, g, bar, nthreads); break;
     case 6: group_bitonic_sort<E, LE, LE + 6, S>(k, gs, g, bar, nthreads); break;
     case 7: group_bitonic_sort<E, LE, LE + 7, S>(k, gs, g, bar, nthreads); break;
     default: group_bitonic_sort<E, LE, LE + 8, S>(k, gs, g, bar, nthreads); break;
     }
+    if (a.profile && g == 0) {
+        const long long t = clock64();
+        atomicAdd(&a.ctrl->cycles[21], static_cast<unsigned long long>(t - t0));
+        atomicAdd(&a.ctrl->cycles[22], static_cast<unsigned long long>(P - len));  // padding slots
+        t0 = t;
+    }
     group_sync(bar, nthreads);
     lay_store<E, LE, S>(k, gs, g, 0);
     group_sync(bar, nthreads);
     typename Tr::K *ok = a.keys[0] + l.off;
     typename Tr::V *ov = a.vals[0] + l.off;
-    for (int i = g; i < len; i += nthreads) LK::store(ok, ov, i, gs[padk<S>(i)]);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int i = g + r * nthreads;
+        if (i < len) LK::store(ok, ov, i, gs[padk<S>(i)]);
+    }
+    if (a.profile && g == 0) atomicAdd(&a.ctrl->cycles[23], static_cast<unsigned long long>(clock64() - t0));
 }
 
 template <class Tr, int E>
@@ -166,6 +193,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
     // threads each, E keys per thread); a part that does not fit is carried
     // over to this CTA's next pass.
     for (;;) {
+        const long long tp = (a.profile && tid == 0) ? clock64() : 0;
         if (tid == 0) {
             int ng = 0, used = 0;
             for (;;) {
@@ -197,6 +225,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
                 if (used == kThreads) break;
             }
             sm.ngroups = ng;
+            if (a.profile) atomicAdd(&a.ctrl->cycles[19], static_cast<unsigned long long>(clock64() - tp));
         }
         __syncthreads();
         const int ng = sm.ngroups;
