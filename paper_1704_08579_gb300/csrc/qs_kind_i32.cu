@@ -4,7 +4,7 @@
 namespace qs {
 
 namespace {
-using Tr = Traits<int32_t, false, 4, 8192, 512>;
+using Tr = Traits<int32_t, false, 8, 8192, 512>;
 using L = Launcher<Tr, 3 * 256 / kDThreads, 2>;  // driver CTAs per SM: register-bound at 80 per thread
 }  // namespace
 
