@@ -185,21 +185,26 @@ __global__ void __launch_bounds__(256) splitter_kernel(const float *__restrict__
     if (t < mlp::kSplit) lb.splitters[t] = spl[t];
 }
 
-// Bucket of sort-space key s among nsplit (<= 255) sorted splitters held in
-// shared memory, padded to 255 with the largest key: number of splitters <= s.
+// Bucket of sort-space key s: the number of splitters <= s.  The 255
+// (padded) splitters are kept in shared memory as a complete binary search
+// tree in breadth-first order (tree[1..255]; node i at depth k holds the
+// sorted splitter (2p+1)*2^(8-k)-1, p = i - 2^(k-1)), so the search is
+// branch-free and the nodes a warp reads at depth k lie in 2^(k-1)
+// consecutive words: no bank conflicts down to depth 6, at most 4-way below.
+// (A search over the sorted array reads addresses 2^(9-k) words apart, up to
+// 8-way conflicted.)  The leaf reached, minus 256, is the count.
 template <class S>
-__device__ __forceinline__ int bucket_of(const S *spl, S s)
+__device__ __forceinline__ int bucket_of(const S *tree, S s)
 {
-    int pos = 0;
+    int i = 1;
 #pragma unroll
-    for (int step = 128; step >= 1; step >>= 1)
-        if (!(s < spl[pos + step - 1])) pos += step;
-    return pos;
+    for (int d = 0; d < 8; ++d) i = 2 * i + (s < tree[i] ? 0 : 1);
+    return i - 256;
 }
 
 template <class Tr>
 struct BucketSmem {
-    typename KeyOps<typename Tr::K>::S spl[255];
+    typename KeyOps<typename Tr::K>::S spl[256];  // search tree, nodes 1..255
     int hist[kWarps][kBuckets];
 };
 
@@ -207,82 +212,153 @@ struct BucketSmem {
 // largest key.  Only a key equal to the largest key can count a pad; such a
 // key belongs to the last bucket anyway, so callers clamp the bucket to nsplit.
 template <class Tr>
-__device__ __forceinline__ void load_splitters(typename KeyOps<typename Tr::K>::S *spl, const LearnedBufs<typename Tr::K> &lb,
+__device__ __forceinline__ void load_splitters(typename KeyOps<typename Tr::K>::S *tree, const LearnedBufs<typename Tr::K> &lb,
                                                int nsplit)
 {
     using Ops = KeyOps<typename Tr::K>;
-    for (int i = threadIdx.x; i < 255; i += kThreads) spl[i] = i < nsplit ? lb.splitters[i] : Ops::s_largest();
+    for (int i = threadIdx.x + 1; i < 256; i += kThreads) {
+        const int k = 31 - __clz(i);  // depth - 1
+        const int r = (2 * (i - (1 << k)) + 1) * (1 << (7 - k)) - 1;  // sorted index
+        tree[i] = r < nsplit ? lb.splitters[r] : Ops::s_largest();
+    }
 }
+
+// Keys per thread per tile of the bucket pass (16 KB tiles).
+template <class K>
+constexpr int bucket_e() { return sizeof(K) == 8 ? 8 : 16; }
 
 template <class Tr>
 __global__ void __launch_bounds__(kThreads) bucket_hist_kernel(const typename Tr::K *__restrict__ keys, int64_t n,
                                                                LearnedBufs<typename Tr::K> lb, int nsplit)
 {
     using Ops = KeyOps<typename Tr::K>;
+    constexpr int E = bucket_e<typename Tr::K>(), TILE = kThreads * E;
     __shared__ BucketSmem<Tr> sm;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5;
     load_splitters<Tr>(sm.spl, lb, nsplit);
     for (int i = tid; i < kWarps * kBuckets; i += kThreads) (&sm.hist[0][0])[i] = 0;
     __syncthreads();
     const int64_t c = blockIdx.x, g = gridDim.x;
     const int64_t lo = c * n / g, hi = (c + 1) * n / g;
-    for (int64_t base = lo; base < hi; base += kThreads) {
-        const int64_t i = base + tid;
-        const bool ok = i < hi;
-        int b = ok ? bucket_of(sm.spl, Ops::to_s(keys[i])) : -1;
-        if (b > nsplit) b = nsplit;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int leader = __ffs(peers) - 1;
-        if (ok && lane == leader) sm.hist[warp][b] += __popc(peers);
+    for (int64_t base = lo; base < hi; base += TILE) {
+        // E independent loads and searches per thread, then one shared-memory
+        // add per key into the warp's own histogram.
+        typename Ops::S k[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int64_t i = base + j * kThreads + tid;
+            k[j] = i < hi ? Ops::to_s(keys[i]) : Ops::s_largest();
+        }
+        int bk[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int bb = bucket_of(sm.spl, k[j]);
+            bk[j] = bb > nsplit ? nsplit : bb;
+        }
+#pragma unroll
+        for (int j = 0; j < E; ++j)
+            if (base + j * kThreads + tid < hi) atomicAdd(&sm.hist[warp][bk[j]], 1);
     }
     __syncthreads();
-    for (int b = tid; b < kBuckets; b += kThreads) {
-        int s = 0;
-        for (int w = 0; w < kWarps; ++w) s += sm.hist[w][b];
-        lb.cnt[static_cast<int64_t>(b) * g + c] = s;
+    for (int bb = tid; bb < kBuckets; bb += kThreads) {
+        int sum = 0;
+        for (int w = 0; w < kWarps; ++w) sum += sm.hist[w][bb];
+        lb.cnt[static_cast<int64_t>(bb) * g + c] = sum;
     }
 }
 
 // One CTA: exclusive scan over (bucket, cta) counts in bucket-major order.
+// Warp w owns the rows (buckets) w, w+32, ...; lane l a contiguous chunk of
+// ceil(ctas/32) counts of a row.  Row totals are scanned once across the CTA,
+// then every count is replaced by its exclusive prefix.
 static __global__ void __launch_bounds__(1024) bucket_scan_kernel(int64_t *__restrict__ cnt, int ctas, LearnedState *st,
                                                            int nsplit, int64_t n, int64_t bound)
 {
-    __shared__ long long part[1024];
-    const int t = threadIdx.x;
-    const int64_t total = static_cast<int64_t>(kBuckets) * ctas;
-    const int64_t per = (total + 1023) / 1024;
-    const int64_t a = t * per, e = a + per < total ? a + per : total;
-    long long s = 0;
-    for (int64_t i = a; i < e; ++i) s += cnt[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the 1024 partial sums
-        const long long v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
+    __shared__ long long tot[kBuckets];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int m = (ctas + 31) / 32;  // counts per lane
+    for (int b = warp; b < kBuckets; b += 32) {
+        const int64_t *row = cnt + static_cast<int64_t>(b) * ctas;
+        long long s = 0;
+        for (int j = lane * m; j < (lane + 1) * m && j < ctas; ++j) s += row[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) tot[b] = s;
     }
-    long long run = t > 0 ? part[t - 1] : 0;
-    for (int64_t i = a; i < e; ++i) {
-        const long long v = cnt[i];
-        cnt[i] = run;
-        if (i % ctas == 0) st->bucket_off[i / ctas] = run;
-        run += v;
+    __syncthreads();
+    if (warp == 0) {  // exclusive scan of the 256 row totals, 8 per lane
+        long long v[kBuckets / 32], sum = 0;
+#pragma unroll
+        for (int i = 0; i < kBuckets / 32; ++i) {
+            v[i] = tot[lane * (kBuckets / 32) + i];
+            sum += v[i];
+        }
+        long long incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        long long run = incl - sum;
+#pragma unroll
+        for (int i = 0; i < kBuckets / 32; ++i) {
+            tot[lane * (kBuckets / 32) + i] = run;
+            run += v[i];
+        }
+    }
+    __syncthreads();
+    for (int b = warp; b < kBuckets; b += 32) {
+        int64_t *row = cnt + static_cast<int64_t>(b) * ctas;
+        long long s = 0;
+        for (int j = lane * m; j < (lane + 1) * m && j < ctas; ++j) s += row[j];
+        long long incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long x = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        long long run = tot[b] + incl - s;
+        for (int j = lane * m; j < (lane + 1) * m && j < ctas; ++j) {
+            const long long v = row[j];
+            row[j] = run;
+            run += v;
+        }
+        if (lane == 0) st->bucket_off[b] = tot[b];
+    }
+    if (t == 0) st->bucket_off[nsplit + 1] = n;
+    __syncthreads();
+    // Bucket statistics, one thread per bucket, reduced over the CTA.
+    __shared__ unsigned long long red[3][32];
+    unsigned long long sz = 0, over = 0, dev = 0;
+    if (t <= nsplit) {
+        sz = static_cast<unsigned long long>(st->bucket_off[t + 1] - st->bucket_off[t]);
+        over = sz > static_cast<unsigned long long>(bound) ? 1 : 0;
+        const long long d = static_cast<long long>(sz) * (nsplit + 1) - n;  // vs the even share n/(nsplit+1)
+        dev = static_cast<unsigned long long>(d < 0 ? -d : d);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long m = __shfl_xor_sync(0xffffffffu, sz, o);
+        sz = m > sz ? m : sz;
+        over += __shfl_xor_sync(0xffffffffu, over, o);
+        dev += __shfl_xor_sync(0xffffffffu, dev, o);
+    }
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = sz;
+        red[1][t >> 5] = over;
+        red[2][t >> 5] = dev;
     }
     __syncthreads();
     if (t == 0) {
-        st->bucket_off[nsplit + 1] = n;
-        unsigned long long mx = 0, over = 0, dev = 0;
-        for (int b = 0; b <= nsplit; ++b) {
-            const unsigned long long sz = static_cast<unsigned long long>(st->bucket_off[b + 1] - st->bucket_off[b]);
-            mx = sz > mx ? sz : mx;
-            over += sz > static_cast<unsigned long long>(bound) ? 1 : 0;
-            const long long d = static_cast<long long>(sz) * (nsplit + 1) - n;  // vs the even share n/(nsplit+1)
-            dev += static_cast<unsigned long long>(d < 0 ? -d : d);
+        unsigned long long mx = 0, ov = 0, dv = 0;
+        for (int w = 0; w < 32; ++w) {
+            mx = red[0][w] > mx ? red[0][w] : mx;
+            ov += red[1][w];
+            dv += red[2][w];
         }
         st->bucket_max = mx;
-        st->bucket_over = over;
-        st->bucket_dev = dev;
+        st->bucket_over = ov;
+        st->bucket_dev = dv;
     }
 }
 
@@ -290,16 +366,21 @@ static_assert(kThreads == kBuckets, "one thread per bucket in the scatter's per-
 
 template <class Tr>
 struct ScatterSmem {
-    typename KeyOps<typename Tr::K>::S spl[255];
-    typename Tr::K keys[kThreads * 8];
-    typename Tr::V vals[Tr::KV ? kThreads * 8 : 1];
-    unsigned char bkt[kThreads * 8];
+    static constexpr int TILE = kThreads * bucket_e<typename Tr::K>();
+    typename KeyOps<typename Tr::K>::S spl[256];  // search tree, nodes 1..255
+    typename Tr::K keys[TILE];
+    typename Tr::V vals[Tr::KV ? TILE : 1];
+    unsigned char bkt[TILE];
     int tcnt[kBuckets];
     int tstart[kBuckets];
     long long cursor[kBuckets];
     int wsum[kWarps];
 };
 
+// Scatter: each tile's keys are ranked inside their buckets with one shared
+// atomic per key, staged in bucket order, and leave the CTA as one
+// contiguous run per (tile, bucket).  The order of keys inside a bucket is
+// not kept (the buckets are sorted afterwards).
 template <class Tr>
 __global__ void __launch_bounds__(kThreads) bucket_scatter_kernel(Args<typename Tr::K, typename Tr::V> a,
                                                                   LearnedBufs<typename Tr::K> lb, int nsplit)
@@ -307,15 +388,15 @@ __global__ void __launch_bounds__(kThreads) bucket_scatter_kernel(Args<typename 
     using K = typename Tr::K;
     using V = typename Tr::V;
     using Ops = KeyOps<K>;
-    constexpr int E = 8, TILE = kThreads * E;
+    constexpr int E = bucket_e<K>(), TILE = kThreads * E;
     __shared__ ScatterSmem<Tr> sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t c = blockIdx.x, g = gridDim.x, n = a.n;
     const int64_t lo = c * n / g, hi = (c + 1) * n / g;
     load_splitters<Tr>(sm.spl, lb, nsplit);
-    for (int b = tid; b < kBuckets; b += kThreads) {
-        sm.cursor[b] = lb.cnt[static_cast<int64_t>(b) * g + c];
-        sm.tcnt[b] = 0;
+    for (int bb = tid; bb < kBuckets; bb += kThreads) {
+        sm.cursor[bb] = lb.cnt[static_cast<int64_t>(bb) * g + c];
+        sm.tcnt[bb] = 0;
     }
     __syncthreads();
     const K *__restrict__ sk = a.keys[0];
@@ -325,27 +406,23 @@ __global__ void __launch_bounds__(kThreads) bucket_scatter_kernel(Args<typename 
     for (int64_t base = lo; base < hi; base += TILE) {
         const int cnt = static_cast<int>(hi - base < TILE ? hi - base : TILE);
         K key[E];
-        V val[E];
+        V val[Tr::KV ? E : 1];
         int bk[E], rk[E];
 #pragma unroll
         for (int j = 0; j < E; ++j) {
             const int q = j * kThreads + tid;
-            const bool ok = q < cnt;
-            key[j] = ok ? sk[base + q] : K(0);
-            if constexpr (Tr::KV) val[j] = ok ? sv[base + q] : 0;
-            int b = ok ? bucket_of(sm.spl, Ops::to_s(key[j])) : -1;
-            if (b > nsplit) b = nsplit;
-            bk[j] = b;
-            const unsigned peers = __match_any_sync(0xffffffffu, b);
-            const int leader = __ffs(peers) - 1;
-            int r0 = 0;
-            if (ok && lane == leader) r0 = atomicAdd(&sm.tcnt[b], __popc(peers));
-            r0 = __shfl_sync(0xffffffffu, r0, leader);
-            rk[j] = r0 + __popc(peers & ((1u << lane) - 1u));
+            key[j] = q < cnt ? sk[base + q] : K(0);
+            if constexpr (Tr::KV) val[j] = q < cnt ? sv[base + q] : 0;
         }
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            const int bb = bucket_of(sm.spl, Ops::to_s(key[j]));
+            bk[j] = j * kThreads + tid < cnt ? (bb > nsplit ? nsplit : bb) : -1;
+        }
+#pragma unroll
+        for (int j = 0; j < E; ++j) rk[j] = bk[j] >= 0 ? atomicAdd(&sm.tcnt[bk[j]], 1) : 0;
         __syncthreads();
-        // exclusive scan of the tile's bucket counts
-        {
+        {  // exclusive scan of the tile's bucket counts (one thread per bucket)
             const int v = sm.tcnt[tid];
             int incl = v;
 #pragma unroll
@@ -369,9 +446,12 @@ __global__ void __launch_bounds__(kThreads) bucket_scatter_kernel(Args<typename 
             sm.bkt[s] = static_cast<unsigned char>(bk[j]);
         }
         __syncthreads();
-        for (int s = tid; s < cnt; s += kThreads) {
-            const int b = sm.bkt[s];
-            const long long d = sm.cursor[b] + (s - sm.tstart[b]);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int s = r * kThreads + tid;
+            if (s >= cnt) continue;
+            const int bb = sm.bkt[s];
+            const long long d = sm.cursor[bb] + (s - sm.tstart[bb]);
             if (d < 0 || d >= n) {
                 lb.st->status = -7;
                 continue;
