@@ -111,6 +111,69 @@ __device__ bool alloc_task(const Args<typename Tr::K, typename Tr::V> &a, int64_
     return true;
 }
 
+// Thread 0: allocates the partition children of a finished task (want[i])
+// with one atomic on the task count and one on the ticket cursor, writes
+// their fields and orders them before any later store of this CTA.
+template <class Tr>
+__device__ void alloc_children(const Args<typename Tr::K, typename Tr::V> &a, const bool (&want)[2],
+                               const int64_t (&off)[2], const int64_t (&len)[2], int src, const uint64_t (&pivot)[2],
+                               const int (&mode)[2], int depth, NewTask (&nt)[2], int (&ok)[2])
+{
+    Ctrl *c = a.ctrl;
+    ok[0] = ok[1] = 0;
+    const int cnt = (want[0] ? 1 : 0) + (want[1] ? 1 : 0);
+    if (cnt == 0) return;
+    if (depth > kMaxDepth) {
+        set_error(c, kErrDepth, depth);
+        return;
+    }
+    int64_t w0[2] = {0, 0}, nti[2] = {0, 0};
+    for (int i = 0; i < 2; ++i)
+        if (want[i]) {
+            w0[i] = off[i] - ((a.key_phase[src] + off[i]) % Tr::VW);
+            nti[i] = (off[i] + len[i] - w0[i] + Tr::T - 1) / Tr::T;
+        }
+    const unsigned long long id = atomicAdd(&c->n_tasks, static_cast<unsigned long long>(cnt));
+    const unsigned long long g = atomicAdd(&c->pool_cursor, static_cast<unsigned long long>(nti[0] + nti[1]));
+    if (id + cnt > static_cast<unsigned long long>(a.task_cap)) {
+        set_error(c, kErrCapacity, 1);
+        return;
+    }
+    if (g + nti[0] + nti[1] > static_cast<unsigned long long>(a.pool_cap)) {
+        set_error(c, kErrCapacity, 2);
+        return;
+    }
+    unsigned long long nid = id, ng = g, keys = 0;
+    for (int i = 0; i < 2; ++i) {
+        if (!want[i]) continue;
+        Task *t = a.tasks + nid;
+        t->off = off[i];
+        t->len = len[i];
+        t->w0 = w0[i];
+        t->pool = static_cast<int64_t>(ng);
+        t->pivot = pivot[i];
+        t->ntiles = static_cast<int32_t>(nti[i]);
+        t->src = src;
+        t->mode = mode[i];
+        t->depth = depth;
+        t->next_tile = 0;
+        t->tiles_done = 0;
+        t->eq = 0;
+        t->lt_total = 0;
+        nt[i].id = static_cast<long long>(nid);
+        nt[i].g0 = static_cast<long long>(ng);
+        nt[i].ntiles = nti[i];
+        ok[i] = 1;
+        keys += static_cast<unsigned long long>(len[i]);
+        ++nid;
+        ng += static_cast<unsigned long long>(nti[i]);
+    }
+    __threadfence();
+    atomicAdd(&c->part_tasks, static_cast<unsigned long long>(cnt));
+    atomicAdd(&c->part_keys, keys);
+    atomicMax(&c->max_depth, static_cast<unsigned long long>(depth));
+}
+
 // Whole CTA (or one warp: first = lane, stride = 32), after alloc_task() and
 // a barrier: makes the task's tickets claimable.
 __device__ __forceinline__ void publish_task(const int32_t *owner_c, const NewTask &nt, int first = -1,
@@ -196,6 +259,7 @@ struct DriverSmem {
     int nt_ok[2];
     int64_t c_off[2], c_len[2];
     int c_kind[2];  // 0 none, 1 finished (equal keys), 2 leaf, 3 partition (sampled pivot), 4 partition ('<=', same pivot)
+    uint64_t pbits[2];  // the children's pivots
     WorkItem wp;    // written tile whose release is deferred
     WorkItem wf;    // task to complete (its last tile was just released)
     int has_prev;   // wp is pending
@@ -760,29 +824,34 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
         }
     }
     __syncthreads();
-    // Children that are partition tasks: pivots first (warp 0), then thread 0
-    // allocates both, then the whole CTA publishes their tickets.
-    uint64_t pbits[2] = {w.pivot, w.pivot};
-    if (tid < 32) {
-        for (int i = 0; i < 2; ++i)
-            if (sm.c_kind[i] == 3)
-                pbits[i] = sample_median<K>(a.keys[dst], sm.c_off[i], sm.c_len[i],
-                                            static_cast<uint64_t>(sm.c_off[i]) * 0x2545F4914F6CDD1Dull + sm.c_len[i]);
+    // Children that are partition tasks: their pivots (warp i samples child
+    // i), then thread 0 allocates both, then the whole CTA publishes their
+    // tickets.
+    const int wi = tid >> 5;
+    if (wi < 2) {
+        uint64_t pb = w.pivot;
+        if (sm.c_kind[wi] == 3)
+            pb = sample_median<K>(a.keys[dst], sm.c_off[wi], sm.c_len[wi],
+                                  static_cast<uint64_t>(sm.c_off[wi]) * 0x2545F4914F6CDD1Dull + sm.c_len[wi]);
+        if ((tid & 31) == 0) sm.pbits[wi] = pb;
     }
+    __syncthreads();
     if (tid == 0) {
-        int nbig = 0;
+        bool want[2];
+        int64_t coff[2], clen[2];
+        uint64_t piv[2];
+        int mode[2];
         for (int i = 0; i < 2; ++i) {
-            sm.nt_ok[i] = 0;
             const int kind = sm.c_kind[i];
-            if (kind == 3 || kind == 4) {
-                sm.nt_ok[i] = alloc_task<Tr>(a, sm.c_off[i], sm.c_len[i], dst, pbits[i],
-                                             kind == 4 ? kModeLessEqual : kModeLess, __ldcg(&t->depth) + 1, sm.nt[i]);
-                nbig += sm.nt_ok[i];
-            } else if (kind == 2) {
-                push_leaf<Tr>(a, sm.c_off[i], sm.c_len[i], dst == 1 ? kLeafScratch : 0);
-            }
+            want[i] = kind == 3 || kind == 4;
+            coff[i] = sm.c_off[i];
+            clen[i] = sm.c_len[i];
+            piv[i] = sm.pbits[i];
+            mode[i] = kind == 4 ? kModeLessEqual : kModeLess;
+            if (kind == 2) push_leaf<Tr>(a, sm.c_off[i], sm.c_len[i], dst == 1 ? kLeafScratch : 0);
         }
-        sm.low_total = nbig;
+        alloc_children<Tr>(a, want, coff, clen, dst, piv, mode, __ldcg(&t->depth) + 1, sm.nt, sm.nt_ok);
+        sm.low_total = sm.nt_ok[0] + sm.nt_ok[1];
     }
     __syncthreads();
     for (int i = 0; i < 2; ++i)
