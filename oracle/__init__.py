@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -56,6 +56,11 @@ def _load():
             lib.oracle_sort_f64.restype = ctypes.c_int
             lib.oracle_sort_kv.argtypes = [vp, vp, i64]
             lib.oracle_sort_kv.restype = ctypes.c_int
+            for name in ("oracle_sort_par_i32", "oracle_sort_par_f64"):
+                getattr(lib, name).argtypes = [vp, i64, ctypes.c_int]
+                getattr(lib, name).restype = ctypes.c_int
+            lib.oracle_sort_par_kv.argtypes = [vp, vp, i64, ctypes.c_int]
+            lib.oracle_sort_par_kv.restype = ctypes.c_int
             lib.oracle_sort_trace_i32.argtypes = [vp, i64, vp, i64, vp]
             lib.oracle_sort_trace_i32.restype = ctypes.c_int
             lib.oracle_select_i32.argtypes = [vp, i64, i64]
@@ -120,6 +125,24 @@ def sort(keys: np.ndarray, values: np.ndarray | None = None):
     else:
         raise TypeError(k.dtype)
     if rc:
+        raise MemoryError("oracle stack")
+    return k
+
+
+def sort_parallel(keys: np.ndarray, values: np.ndarray | None = None, threads: int | None = None):
+    """Sorted copies like sort(), computed by the task-parallel oracle (same result bit for bit)."""
+    lib = _load()
+    t = threads or os.cpu_count() or 1
+    k = np.array(keys, copy=True, order="C")
+    if values is not None:
+        v = np.array(values, dtype=np.int32, copy=True, order="C")
+        if lib.oracle_sort_par_kv(_p(k), _p(v), k.size, t):
+            raise MemoryError("oracle stack")
+        return k, v
+    fn = lib.oracle_sort_par_i32 if k.dtype == np.int32 else lib.oracle_sort_par_f64
+    if k.dtype not in (np.int32, np.float64):
+        raise TypeError(k.dtype)
+    if fn(_p(k), k.size, t):
         raise MemoryError("oracle stack")
     return k
 

@@ -24,6 +24,9 @@
 //             all-equal input, e.g. the few-unique workloads).
 //       Key/value sorting (Section III-D) applies every key move to the value
 //       array too.
+//   oracle_sort_par_{i32,f64,kv}   the same, with the two sides of large
+//       ranges handed to separate threads (the paper's own suggestion of a
+//       task-parallel recursion); bit-for-bit the sequential result.
 //   oracle_select_{i32,f64}        k-th smallest key by repeated Appendix A
 //       steps (quickselect); used to pick a true-median pivot.
 //   oracle_mlp_*, oracle_bucket_*  the learned-splitter growth line (no
@@ -35,6 +38,7 @@
 #include <cstdint>
 #include <cmath>
 #include <cstdlib>
+#include <thread>
 
 namespace {
 
@@ -126,13 +130,13 @@ struct Range {
 // records each chosen pivot (in the order chosen).  Returns 0, or -1 when the
 // stack cannot grow.
 template <class K, class V>
-int quicksort(K *a, V &vals, int64_t n, double *trace, int64_t trace_cap, int64_t *ntrace)
+int quicksort_range(K *a, V &vals, int64_t first, int64_t last, double *trace, int64_t trace_cap, int64_t *ntrace)
 {
-    if (n < 2) return 0;
+    if (last <= first) return 0;
     int64_t cap = 64, size = 0;
     Range *stack = static_cast<Range *>(std::malloc(sizeof(Range) * cap));
     if (!stack) return -1;
-    stack[size++] = Range{0, n - 1};
+    stack[size++] = Range{first, last};
     while (size > 0) {
         Range r = stack[--size];
         int64_t left = r.left, right = r.right;
@@ -166,6 +170,32 @@ int quicksort(K *a, V &vals, int64_t n, double *trace, int64_t trace_cap, int64_
     }
     std::free(stack);
     return 0;
+}
+
+template <class K, class V>
+int quicksort(K *a, V &vals, int64_t n, double *trace, int64_t trace_cap, int64_t *ntrace)
+{
+    return quicksort_range(a, vals, int64_t(0), n - 1, trace, trace_cap, ntrace);
+}
+
+// The same Appendix A steps with the two sides of large ranges sorted by
+// separate threads.  Every step touches only its own range, so the order in
+// which disjoint ranges are processed cannot change the result: the output
+// is bit-for-bit the sequential one (keys and values).
+template <class K, class V>
+int quicksort_parallel(K *a, V vals, int64_t left, int64_t right, int threads)
+{
+    if (threads <= 1 || right - left < (int64_t(1) << 16)) {
+        V v = vals;
+        return quicksort_range(a, v, left, right, nullptr, 0, nullptr);
+    }
+    int64_t lt_end, gt_begin;
+    quicksort_step(a, vals, left, right, &lt_end, &gt_begin);
+    int rc_low = 0;
+    std::thread low([&] { rc_low = quicksort_parallel(a, vals, left, lt_end - 1, threads / 2); });
+    const int rc_high = quicksort_parallel(a, vals, gt_begin, right, threads - threads / 2);
+    low.join();
+    return rc_low | rc_high;
 }
 
 template <class K>
@@ -222,6 +252,21 @@ int oracle_sort_kv(int32_t *keys, int32_t *vals, int64_t n)
 {
     Values v{vals};
     return quicksort(keys, v, n, nullptr, 0, nullptr);
+}
+
+int oracle_sort_par_i32(int32_t *a, int64_t n, int threads)
+{
+    return n < 2 ? 0 : quicksort_parallel(a, NoValues{}, int64_t(0), n - 1, threads);
+}
+
+int oracle_sort_par_f64(double *a, int64_t n, int threads)
+{
+    return n < 2 ? 0 : quicksort_parallel(a, NoValues{}, int64_t(0), n - 1, threads);
+}
+
+int oracle_sort_par_kv(int32_t *keys, int32_t *vals, int64_t n, int threads)
+{
+    return n < 2 ? 0 : quicksort_parallel(keys, Values{vals}, int64_t(0), n - 1, threads);
 }
 
 int oracle_sort_trace_i32(int32_t *a, int64_t n, double *trace, int64_t trace_cap, int64_t *ntrace)

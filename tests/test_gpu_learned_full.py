@@ -3,19 +3,17 @@
 (lognormal(0, 2)), generated on the device with the same recipes and
 SplitMix64 streams as the host generators.
 
-At this size the checks are properties that hold at any size plus sampled
-order statistics: the output is non-decreasing, a permutation of the input
-(order-independent 64-bit hash of the multiset), bit-for-bit the output of
-the plain sort of the same input, and output[k] equals the oracle's k-th
-smallest key for sampled k.  Sampled splitters, a model trained briefly with
+At this size the checks are: the whole output against the oracle's sort (the
+task-parallel oracle, bit-for-bit the sequential one), bit-for-bit the output
+of the plain sort of the same input, non-decreasing and a permutation of the
+input (order-independent 64-bit hash of the multiset).  Sampled splitters, a model trained briefly with
 the library's kernels and a deliberately bad model (one bucket takes almost
 everything, so the size bound sends it to the plain method) are covered.
 """
-import numpy as np
 import pytest
 
 import oracle
-from qs_testutil import qs_gpu
+from qs_testutil import assert_keys_equal, qs_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -77,7 +75,6 @@ def test_full_learned_sort(name, trained):
 
     qs = qs_gpu()
     x, kind = _make(name)
-    n = x.numel()
     h_in = _hash64(x)
     ref = x.clone()
     qs.sort(ref)
@@ -96,7 +93,4 @@ def test_full_learned_sort(name, trained):
     got = ref.cpu().numpy()
     del x, ref
     torch.cuda.empty_cache()
-    rng = np.random.default_rng(9)
-    for k in [0, n // 2] + [int(q) for q in rng.integers(0, n, 1)]:
-        exp = oracle.select(host, k)
-        assert got[k] == exp, (k, got[k], exp)
+    assert_keys_equal(got, oracle.sort_parallel(host))

@@ -169,3 +169,17 @@ def test_synth_properties():
     np.testing.assert_array_equal(synth.uniform_i32(1000, 9)[500:], synth.uniform_i32(1000, 9)[500:])
     keys, offs = synth.segments_i32(50)
     assert offs[0] == 0 and offs[-1] == keys.size and np.all(np.diff(offs) >= 16)
+
+
+@pytest.mark.parametrize("threads", [1, 2, 3, 16])
+def test_parallel_oracle_equals_sequential(threads):
+    """The task-parallel oracle runs the same Appendix A steps: identical output."""
+    for n, seed in ((0, 1), (1, 2), (70000, 3), ((1 << 18) + 11, 4)):
+        x = synth.uniform_f64(n, seed)
+        assert np.array_equal(oracle.sort_parallel(x, threads=threads).view(np.int64), oracle.sort(x).view(np.int64))
+        y = synth.mod_i32(n, seed, 37)
+        assert np.array_equal(oracle.sort_parallel(y, threads=threads), oracle.sort(y))
+        k, v = synth.kv_config("mod1000", n, seed)
+        pk, pv = oracle.sort_parallel(k, v, threads=threads)
+        sk, sv = oracle.sort(k, v)
+        assert np.array_equal(pk, sk) and np.array_equal(pv, sv)
