@@ -469,6 +469,45 @@ def _learned(torch, qs, stream, steps=3):
     return out
 
 
+def _leaf_sweep(torch, qs, stream, total=1 << 24, reps=3):
+    """Many independent arrays of one size n in one segmented-sort call, for n
+    from 2 up past the leaf threshold: the leaf network's throughput per array
+    size (and where the partition path takes over)."""
+    out = {}
+    sizes = [2, 8, 32, 100, 512, 513, 1000, 2048, 3000, 4096, 6000, 8192, 12000, 16384, 65536]
+    for kind, dtype in (("i32", torch.int32), ("f64", torch.float64)):
+        rows = []
+        for n in sizes:
+            nseg = max(1, total // n)
+            m = nseg * n
+            if dtype == torch.int32:
+                keys = torch.from_numpy(synth.uniform_i32(m, 0x1EAF)).to("cuda")
+            else:
+                keys = torch.from_numpy(synth.uniform_f64(m, 0x1EAF)).to("cuda")
+            offs = torch.arange(0, nseg + 1, dtype=torch.int64, device="cuda") * n
+            work = torch.empty_like(keys)
+            times = []
+            for r in range(reps + 1):
+                work.copy_(keys)
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    a.record(stream)
+                    qs.sort_segmented(work, offs, stream=stream)
+                    b.record(stream)
+                b.synchronize()
+                if r:
+                    times.append(a.elapsed_time(b))
+            ms = statistics.median(times)
+            rows.append({"n": n, "arrays": nseg, "ms": ms, "gkeys_s": m / (ms / 1e3) / 1e9,
+                         "ns_per_array": ms * 1e6 / nseg})
+            del keys, work, offs
+        out[kind] = rows
+    torch.cuda.empty_cache()
+    return out
+
+
 def _extras(torch, qs, stream, hbm_peak):
     out = []
     n = N_KEYS
@@ -539,7 +578,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--op", choices=["sort", "partition", "learned", "batched"], default="sort",
+    ap.add_argument("--op", choices=["sort", "partition", "learned", "batched", "leafsweep"], default="sort",
                     help="partition / learned / batched: that measurement alone (not the benchmark line)")
     ap.add_argument("--log2n", type=int, default=LOG2N,
                     help="log2 of the keys per sort (28 = the benchmark workload; smaller only for profiling)")
@@ -552,7 +591,7 @@ def main():
         return run_reference(args)
     if args.op == "partition":
         return run_partition_only(args)
-    if args.op in ("learned", "batched"):
+    if args.op in ("learned", "batched", "leafsweep"):
         return run_section(args.op)
     return run_ours(args)
 
@@ -568,7 +607,7 @@ def run_section(name: str) -> int:
     qs_build.build()
     qs.load()
     stream = torch.cuda.Stream()
-    res = _learned(torch, qs, stream) if name == "learned" else _batched(torch, qs, stream)
+    res = {"learned": _learned, "batched": _batched, "leafsweep": _leaf_sweep}[name](torch, qs, stream)
     print(json.dumps({"section": name, name: res}), flush=True)
     return 0
 
