@@ -1043,7 +1043,8 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(Args<typename Tr::K, ty
 }
 
 // ---------------------------------------------------------------------------
-// Segmented sort setup: one warp per segment.  A segment of at most leaf_max
+// Segmented sort setup: one lane per segment for the leaves, one warp per
+// partition task.  A segment of at most leaf_max
 // keys goes straight to the leaf list; a larger one becomes a partition task
 // with a sampled pivot.  Offsets are checked on the device (0 <= off[i] <=
 // off[i+1] <= n); a bad table records QS_ERR_INVALID_ARG.
@@ -1053,27 +1054,71 @@ __global__ void __launch_bounds__(kThreads) setup_segments_kernel(Args<typename 
 {
     using K = typename Tr::K;
     const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
     const long long warp = (static_cast<long long>(blockIdx.x) * kThreads + threadIdx.x) >> 5;
     const long long nwarps = (static_cast<long long>(gridDim.x) * kThreads) >> 5;
+    const int src = a.seg_src;
+    // 32 segments per warp step, one per lane: the leaves of a step are listed
+    // with one reservation per side (a step of tiny segments costs a few
+    // atomics, not a few per segment).
+    for (long long s0 = warp * 32; s0 < a.nseg; s0 += nwarps * 32) {
+        const long long i = s0 + lane;
+        int kind = 0;  // 0 nothing, 1 small leaf, 2 large leaf, 3 partition task
+        int64_t off = 0, len = 0;
+        if (i < a.nseg) {
+            off = a.seg_off[i];
+            const int64_t end = a.seg_off[i + 1];
+            if (off < 0 || end < off || end > a.n) {
+                set_error(a.ctrl, -1, static_cast<int>(i));
+            } else {
+                len = end - off;
+                if (len <= 1) {  // already sorted; from scratch it only has to move home
+                    if (len == 1 && src) {
+                        a.keys[0][off] = a.keys[1][off];
+                        if constexpr (Tr::KV) a.vals[0][off] = a.vals[1][off];
+                    }
+                } else if (len <= a.leaf_max) {
+                    kind = len <= a.small_max ? 1 : 2;
+                } else {
+                    kind = 3;
+                }
+            }
+        }
+        const unsigned sm_mask = __ballot_sync(0xffffffffu, kind == 1);
+        const unsigned lg_mask = __ballot_sync(0xffffffffu, kind == 2);
+        long long base_s = -1, base_l = -1;
+        if (lane == 0) {
+            if (sm_mask) base_s = reserve_leaves<Tr>(a, __popc(sm_mask), true);
+            if (lg_mask) base_l = reserve_leaves<Tr>(a, __popc(lg_mask), false);
+        }
+        base_s = __shfl_sync(0xffffffffu, base_s, 0);
+        base_l = __shfl_sync(0xffffffffu, base_l, 0);
+        if ((kind == 1 && base_s >= 0) || (kind == 2 && base_l >= 0)) {
+            Leaf l;
+            l.off = off;
+            l.len = static_cast<int32_t>(len);
+            l.flags = src ? kLeafScratch : 0;
+            // the small side grows downward from the end of the list
+            const long long at = kind == 1 ? base_s - __popc(sm_mask & below) : base_l + __popc(lg_mask & below);
+            a.leaves[at] = l;
+        }
+        unsigned long long nk = (kind == 1 || kind == 2) ? static_cast<unsigned long long>(len) : 0ull;
+        unsigned long long np = (kind == 1 || kind == 2) ? 1ull : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            nk += __shfl_xor_sync(0xffffffffu, nk, o);
+            np += __shfl_xor_sync(0xffffffffu, np, o);
+        }
+        if (lane == 0 && np) {
+            atomicAdd(&a.ctrl->leaf_parts, np);
+            atomicAdd(&a.ctrl->leaf_keys, nk);
+        }
+    }
+    // Partition tasks, one warp each (they are few; each needs a pivot sample).
     for (long long i = warp; i < a.nseg; i += nwarps) {
         const int64_t off = a.seg_off[i], end = a.seg_off[i + 1];
-        if (off < 0 || end < off || end > a.n) {
-            if (lane == 0) set_error(a.ctrl, -1, static_cast<int>(i));
-            continue;
-        }
+        if (off < 0 || end < off || end > a.n || end - off <= a.leaf_max) continue;
         const int64_t len = end - off;
-        const int src = a.seg_src;
-        if (len <= 1) {  // already sorted; from scratch it only has to move home
-            if (len == 1 && src && lane == 0) {
-                a.keys[0][off] = a.keys[1][off];
-                if constexpr (Tr::KV) a.vals[0][off] = a.vals[1][off];
-            }
-            continue;
-        }
-        if (len <= a.leaf_max) {
-            if (lane == 0) push_leaf<Tr>(a, off, len, src ? kLeafScratch : 0);
-            continue;
-        }
         const uint64_t pbits =
             sample_median<K>(a.keys[src], off, len, static_cast<uint64_t>(off) * 0x9E3779B97F4A7C15ull + len);
         NewTask nt;
