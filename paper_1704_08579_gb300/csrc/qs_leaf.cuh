@@ -248,27 +248,43 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
         }
         __syncthreads();
     }
-    // Small parts: one warp each.
+    // Small parts: one warp each, claimed in batches of up to 32 when there
+    // are many (one atomic and one coalesced read of the descriptors per
+    // batch), one at a time when there are few (so every warp gets work).
+    const long long nwarps_all = static_cast<long long>(gridDim.x) * (kThreads / 32);
+    const long long per_warp = n_small / (8 * nwarps_all);
+    const int batch = per_warp >= 32 ? 32 : (per_warp < 1 ? 1 : static_cast<int>(per_warp));
     for (;;) {
-        long long idx = 0;
-        if (lane == 0) idx = static_cast<long long>(atomicAdd(&c->claim_small, 1ull));
-        idx = __shfl_sync(0xffffffffu, idx, 0);
-        if (idx >= n_small) break;
-        const Leaf l = a.leaves[a.leaf_cap - 1 - idx];
-        if (!leaf_ok<Tr>(a, l, true)) continue;
-        if (l.flags & kLeafFinal) {
-            for (int i = lane; i < l.len; i += 32) {
-                a.keys[0][l.off + i] = a.keys[1][l.off + i];
-                if constexpr (Tr::KV) a.vals[0][l.off + i] = a.vals[1][l.off + i];
+        long long base = 0;
+        if (lane == 0) base = static_cast<long long>(atomicAdd(&c->claim_small, static_cast<unsigned long long>(batch)));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_small) break;
+        const int cnt = static_cast<int>(n_small - base < batch ? n_small - base : batch);
+        Leaf mine;
+        mine.off = 0;
+        mine.len = 0;
+        mine.flags = 0;
+        if (lane < cnt) mine = a.leaves[a.leaf_cap - 1 - (base + lane)];
+        for (int q = 0; q < cnt; ++q) {
+            Leaf l;
+            l.off = __shfl_sync(0xffffffffu, mine.off, q);
+            l.len = __shfl_sync(0xffffffffu, mine.len, q);
+            l.flags = __shfl_sync(0xffffffffu, mine.flags, q);
+            if (!leaf_ok<Tr>(a, l, true)) continue;
+            if (l.flags & kLeafFinal) {
+                for (int i = lane; i < l.len; i += 32) {
+                    a.keys[0][l.off + i] = a.keys[1][l.off + i];
+                    if constexpr (Tr::KV) a.vals[0][l.off + i] = a.vals[1][l.off + i];
+                }
+                continue;
             }
-            continue;
+            const int len = l.len;
+            if (len <= 32) warp_leaf<Tr, 1>(a, l);
+            else if (len <= 64) warp_leaf<Tr, 2>(a, l);
+            else if (len <= 128) warp_leaf<Tr, 4>(a, l);
+            else if (len <= 256) warp_leaf<Tr, 8>(a, l);
+            else warp_leaf<Tr, (Tr::SMALL >= 512 ? 16 : Tr::SMALL / 32)>(a, l);
         }
-        const int len = l.len;
-        if (len <= 32) warp_leaf<Tr, 1>(a, l);
-        else if (len <= 64) warp_leaf<Tr, 2>(a, l);
-        else if (len <= 128) warp_leaf<Tr, 4>(a, l);
-        else if (len <= 256) warp_leaf<Tr, 8>(a, l);
-        else warp_leaf<Tr, (Tr::SMALL >= 512 ? 16 : Tr::SMALL / 32)>(a, l);
     }
 }
 
