@@ -251,7 +251,7 @@ typedef struct {
      * [2] comparing and counting, [3] the look-back, [4] staging and storing,
      * [5] releasing the tile, [6] completing tasks (pivots, children);
      * [7] = tiles processed; [8] cycles inside the look-back proper (warp 0),
-     * [9] cycles warps 1..7 waited for the prefetched tile, [10] look-back
+     * [9] cycles the middle warps waited for the prefetched tile, [10] look-back
      * windows of 32 words read, [11] re-reads of unpublished words;
      * [13] claiming and resolving the next ticket and issuing its load
      * (thread 0); [12], [14], [15] look-back phase as seen by the counting

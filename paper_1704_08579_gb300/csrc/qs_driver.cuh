@@ -19,10 +19,12 @@
 // what one pass with a left write cursor and a right write cursor produces
 // (the paper's left_w / right_w).
 //
-// The CTA that processes the last tile of a task waits until every other tile
-// of the task has released its stores, then completes the task: it picks the
-// pivots of the children (median of 64 sampled keys) and queues them, or lists
-// them for the Bitonic kernel when they hold at most leaf_max keys.
+// Every written tile is released (its stores ordered before an acq_rel add on
+// the task's tile counter); the CTA whose release is the task's last, in
+// whatever order the tiles finish, completes the task without waiting for
+// anyone: it picks the pivots of the children (median of 64 sampled keys) and
+// queues them, or lists them for the Bitonic kernel when they hold at most
+// leaf_max keys.
 #pragma once
 
 #include "qs_bitonic.cuh"
@@ -231,7 +233,7 @@ struct WorkItem {
     int ntiles;
     int src, mode;
     int full;   // tile lies entirely inside the task: TMA bulk load
-    int a_pub;  // its look-back aggregate was already published (early count)
+    int a_pub;  // its look-back aggregate was already published (while it was prefetched)
     int64_t off, len, w0, pool;
     uint64_t pivot;
 };
@@ -249,7 +251,7 @@ struct DriverSmem {
     long long first;
     int low_total;
     int eq_total;
-    int next_low;  // early count of the prefetched tile (warps 1..7)
+    int next_low;  // lower-side count of the prefetched tile (middle warps)
     long long tm[kProfSlots];  // per-phase cycles and counters (profiling on)
     int last;
     int abort;
@@ -490,10 +492,11 @@ __device__ __forceinline__ int count_low_any(const typename Tr::K *buf, uint64_t
 
 // ---------------------------------------------------------------------------
 // Release of a written tile (one thread, after a CTA barrier that follows the
-// tile's stores): its pivot-equal count, a fence, then the task's tile
-// counter.  The tile that arrives last completes the task, so no CTA ever
-// waits for the others.  The release is deferred into the next tile (see
-// partition_tile), where the fence finds the stores already drained.
+// tile's stores): its pivot-equal count, then an acq_rel add on the task's
+// tile counter (it releases the stores; the last adder acquires everyone's).
+// The tile that arrives last completes the task, so no CTA ever waits for
+// the others.  The release is deferred into the next tile (see
+// partition_tile), where the stores have had time to drain.
 // ---------------------------------------------------------------------------
 template <class Tr>
 __device__ __forceinline__ void release_prev(const Args<typename Tr::K, typename Tr::V> &a, DriverSmem<Tr> &sm)
