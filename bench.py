@@ -397,7 +397,7 @@ def _batched(torch, qs, stream, nseg=20_000, steps=3):
         out[kind] = {"workload": "%d %s arrays, sizes log-uniform [16, 2^18], %d keys" % (nseg, kind, n),
                      "batched_ms": ms_batched, "batched_gkeys_s": n / (ms_batched / 1e3) / 1e9,
                      "plain_per_array_ms": ms_plain, "plain_gkeys_s": n / (ms_plain / 1e3) / 1e9,
-                     "speedup": ms_plain / ms_batched, "tuned": {k: tuned[k] for k in ("leaf_max", "small_max")},
+                     "speedup": ms_plain / ms_batched, "tuned": {k: tuned[k] for k in ("leaf_max", "small_max", "driver_items")},
                      "batched_sorted": ok}
         del dk, dv, pk, pv
         torch.cuda.empty_cache()

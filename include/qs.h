@@ -287,6 +287,11 @@ int qs_get_stats(qs_stats *out);
  *                        values are clamped to it.
  *   QS_OPT_SMALL_MAX     parts of at most this many keys (power of two, >= 32)
  *                        are sorted by one warp; 0 = the compiled maximum 512.
+ *   QS_OPT_DRIVER_ITEMS  keys per thread of a partition tile: each kind has a
+ *                        wide (default) and a narrow compiled variant (i32
+ *                        32 / 16, f64 16 / 8, kv 16 / 8); the narrow value
+ *                        selects the narrow one, any other value (0 included)
+ *                        the wide one.
  * The tuning options are what the autotuner (paper_1704_08579_gb300.autotune)
  * searches.
  */
@@ -296,7 +301,8 @@ enum {
     QS_OPT_TASK_CAP = 3,
     QS_OPT_DRIVER_CTAS = 4,
     QS_OPT_LEAF_MAX = 5,
-    QS_OPT_SMALL_MAX = 6
+    QS_OPT_SMALL_MAX = 6,
+    QS_OPT_DRIVER_ITEMS = 7
 };
 int qs_set_option(int option, int64_t value);
 

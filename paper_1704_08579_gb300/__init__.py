@@ -30,7 +30,8 @@ STATUS = {
     -5: "QS_ERR_TIMEOUT", -6: "QS_ERR_CAPACITY", -7: "QS_ERR_INTERNAL",
 }
 KIND = {"i32": 0, "f64": 1, "kv": 2}
-OPTION = {"profile": 1, "wait_limit_ns": 2, "task_cap": 3, "driver_ctas": 4, "leaf_max": 5, "small_max": 6}
+OPTION = {"profile": 1, "wait_limit_ns": 2, "task_cap": 3, "driver_ctas": 4, "leaf_max": 5, "small_max": 6,
+          "driver_items": 7}
 
 _lib = None
 _lock = threading.Lock()

@@ -1,9 +1,11 @@
 """Autotuner for the run-time knobs of the sort: the leaf threshold (largest
-part handed to the Bitonic kernel, QS_OPT_LEAF_MAX) and the one-warp threshold
-(QS_OPT_SMALL_MAX).  Each candidate is timed on the caller's own data with
-CUDA events (a fresh copy of the input per run, so every run sorts the same
-unsorted data); the fastest is kept, applied with qs_set_option, and recorded
-in a JSON cache keyed by GPU name and workload signature.
+part handed to the Bitonic kernel, QS_OPT_LEAF_MAX), the one-warp threshold
+(QS_OPT_SMALL_MAX) and the keys per thread of a partition tile
+(QS_OPT_DRIVER_ITEMS, one of the two compiled tile variants).  Each candidate
+is timed on the caller's own data with CUDA events (a fresh copy of the input
+per run, so every run sorts the same unsorted data); the fastest is kept,
+applied with qs_set_option, and recorded in a JSON cache keyed by GPU name and
+workload signature.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ CACHE_DIR = os.path.join(HERE, "tuning")
 
 LEAF_CHOICES = {"i32": (2048, 4096, 8192), "f64": (1024, 2048, 4096), "kv": (1024, 2048, 4096)}
 SMALL_CHOICES = (128, 256, 512)
+ITEMS_CHOICES = {"i32": (32, 16), "f64": (16, 8), "kv": (16, 8)}  # wide (default), narrow
 
 
 def _cache_path(gpu_name: str) -> str:
@@ -49,12 +52,14 @@ def signature(kind: str, n: int, nseg: int) -> str:
 def apply(cfg: dict) -> None:
     qs.set_option("leaf_max", int(cfg.get("leaf_max", 0)))
     qs.set_option("small_max", int(cfg.get("small_max", 0)))
+    qs.set_option("driver_items", int(cfg.get("driver_items", 0)))
 
 
 def tune(keys, offsets=None, values=None, reps: int = 2, use_cache: bool = True, stream=None) -> dict:
-    """Tunes (leaf_max, small_max) for sorting `keys` (CUDA tensor), segmented by
-    `offsets` if given; returns {"leaf_max", "small_max", "ms", "table"} and
-    leaves the winner applied.  The input tensors are not modified."""
+    """Tunes (leaf_max, small_max, driver_items) for sorting `keys` (CUDA
+    tensor), segmented by `offsets` if given; returns {"leaf_max", "small_max",
+    "driver_items", "ms", "table"} and leaves the winner applied.  The input
+    tensors are not modified."""
     import torch
 
     kind = "kv" if values is not None else ("i32" if keys.dtype == torch.int32 else "f64")
@@ -69,32 +74,42 @@ def tune(keys, offsets=None, values=None, reps: int = 2, use_cache: bool = True,
     work_k = torch.empty_like(keys)
     work_v = torch.empty_like(values) if values is not None else None
     table = []
+
+    def timed(cfg):
+        apply(cfg)
+        times = []
+        for _ in range(reps + 1):  # the first run warms up (and captures the graph)
+            work_k.copy_(keys)
+            if work_v is not None:
+                work_v.copy_(values)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                if offsets is None:
+                    qs.sort(work_k, work_v, stream=stream)
+                else:
+                    qs.sort_segmented(work_k, offsets, work_v, stream=stream)
+                b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        row = dict(cfg, ms=statistics.median(times[1:]))
+        table.append(row)
+        return row
+
+    # Thresholds with the wide tile, then the tile variants at the best thresholds.
     for leaf in LEAF_CHOICES[kind]:
         for small in SMALL_CHOICES:
-            if small > leaf:
-                continue
-            apply({"leaf_max": leaf, "small_max": small})
-            times = []
-            for _ in range(reps + 1):  # the first run warms up (and captures the graph)
-                work_k.copy_(keys)
-                if work_v is not None:
-                    work_v.copy_(values)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                with torch.cuda.stream(stream):
-                    a.record(stream)
-                    if offsets is None:
-                        qs.sort(work_k, work_v, stream=stream)
-                    else:
-                        qs.sort_segmented(work_k, offsets, work_v, stream=stream)
-                    b.record(stream)
-                b.synchronize()
-                times.append(a.elapsed_time(b))
-            table.append({"leaf_max": leaf, "small_max": small, "ms": statistics.median(times[1:])})
+            if small <= leaf:
+                timed({"leaf_max": leaf, "small_max": small, "driver_items": ITEMS_CHOICES[kind][0]})
     best = min(table, key=lambda r: r["ms"])
-    result = {"leaf_max": best["leaf_max"], "small_max": best["small_max"], "ms": best["ms"], "table": table}
+    for items in ITEMS_CHOICES[kind][1:]:
+        timed({"leaf_max": best["leaf_max"], "small_max": best["small_max"], "driver_items": items})
+    best = min(table, key=lambda r: r["ms"])
+    result = {"leaf_max": best["leaf_max"], "small_max": best["small_max"], "driver_items": best["driver_items"],
+              "ms": best["ms"], "table": table}
     apply(result)
     if use_cache:
-        cache[sig] = {k: result[k] for k in ("leaf_max", "small_max", "ms")}
+        cache[sig] = {k: result[k] for k in ("leaf_max", "small_max", "driver_items", "ms")}
         _store_cache(gpu, cache)
     return result

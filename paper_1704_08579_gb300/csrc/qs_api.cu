@@ -27,6 +27,7 @@ std::atomic<int64_t> g_task_cap{0};
 std::atomic<int64_t> g_driver_ctas{0};
 std::atomic<int64_t> g_leaf_max{0};   // 0 = the kind's compiled maximum
 std::atomic<int64_t> g_small_max{0};  // 0 = the kind's compiled maximum
+std::atomic<int64_t> g_driver_items{0};  // 0 = the wide partition tile
 
 constexpr int64_t kMaxN = 1ll << 38;
 
@@ -51,7 +52,7 @@ struct Workspace {
     std::mutex mu;
     bool init = false;
     int sms = 0;
-    int occ[3][2] = {};
+    int occ[3][3] = {};  // per kind: driver (wide tile), leaf, driver (narrow tile)
     void *scratch_k = nullptr, *scratch_v = nullptr;
     size_t scratch_k_bytes = 0, scratch_v_bytes = 0;
     void *stage_k = nullptr, *stage_v = nullptr;
@@ -136,7 +137,7 @@ int ws_init(Workspace &w)
     e = cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     for (int k = 0; k < 3; ++k)
-        for (int which = 0; which < 2; ++which) {
+        for (int which = 0; which < 3; ++which) {
             e = static_cast<cudaError_t>(occupancy_of(k, which, &w.occ[k][which]));
             if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
             if (w.occ[k][which] < 1) return fail(QS_ERR_INTERNAL, "kernel cannot be resident (kind %d)", k);
@@ -377,7 +378,9 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.stream = s;
     const int64_t ctas = g_driver_ctas.load();
-    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][0];
+    cfg.items = static_cast<int>(g_driver_items.load());
+    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas)
+                               : w.sms * w.occ[kind][cfg.items == limits_of(kind).items_narrow ? 2 : 0];
     cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];
     cfg.profile = g_profile.load();
     for (int i = 0; i < 6; ++i) cfg.ev[i] = w.ev[i];
@@ -398,9 +401,9 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
         // kernel, leaf kernel, status read-back) per argument set.
         cfg.profile = 0;
         char key[320];
-        snprintf(key, sizeof(key), "%d:%p:%p:%p:%lld:%lld:%lld:%lld:%d:%d:%llu", kind, (void *)keys, (void *)vals,
+        snprintf(key, sizeof(key), "%d:%p:%p:%p:%lld:%lld:%lld:%lld:%d:%d:%d:%llu", kind, (void *)keys, (void *)vals,
                  (const void *)seg_off, (long long)n, (long long)nseg, (long long)a.leaf_max, (long long)a.small_max,
-                 cfg.grid_driver, cfg.grid_leaf, (unsigned long long)a.wait_limit_ns);
+                 cfg.grid_driver, cfg.grid_leaf, cfg.items, (unsigned long long)a.wait_limit_ns);
         cudaGraphExec_t exec = nullptr;
         for (auto &g : w.graphs)
             if (g.key == key) exec = g.exec;
@@ -598,7 +601,9 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.stream = s;
     const int64_t ctas = g_driver_ctas.load();
-    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][0];
+    cfg.items = static_cast<int>(g_driver_items.load());
+    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas)
+                               : w.sms * w.occ[kind][cfg.items == limits_of(kind).items_narrow ? 2 : 0];
     cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];
     cfg.profile = g_profile.load();
     for (int i = 0; i < 6; ++i) cfg.ev[i] = w.ev[i];
@@ -847,6 +852,10 @@ int qs_set_option(int option, int64_t value)
     case QS_OPT_DRIVER_CTAS:
         if (value < 0 || value > (1 << 20)) return QS_ERR_INVALID_ARG;
         g_driver_ctas = value;
+        return QS_OK;
+    case QS_OPT_DRIVER_ITEMS:
+        if (value < 0 || value > 64) return QS_ERR_INVALID_ARG;
+        g_driver_items = value;
         return QS_OK;
     case QS_OPT_LEAF_MAX:
     case QS_OPT_SMALL_MAX:

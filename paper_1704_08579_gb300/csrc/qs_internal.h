@@ -110,6 +110,7 @@ struct LaunchCfg {
     void *stream;
     int grid_driver;
     int grid_leaf;
+    int items;  // keys per thread of a partition tile: the narrow variant's, or any other value for the wide one
     int profile;
     void *ev[6];  // cudaEvent_t when profiling
 };
@@ -150,8 +151,9 @@ struct LearnedCall {
 };
 
 struct KernelLimits {
-    int64_t leaf_max, small_max, tile;
+    int64_t leaf_max, small_max, tile;  // tile: the smaller of the two partition tile variants
     size_t driver_smem, leaf_smem;
+    int items_wide, items_narrow;       // keys per thread of the two partition tile variants
 };
 
 // Per-kind entry points implemented in qs_kind_{i32,f64,kv}.cu.  They enqueue

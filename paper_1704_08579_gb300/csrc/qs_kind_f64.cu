@@ -4,13 +4,27 @@
 namespace qs {
 
 namespace {
+// Two partition tile variants (items per thread); the wide one is the default,
+// the narrow one is chosen per call by QS_OPT_DRIVER_ITEMS (the autotuner).
 using Tr = Traits<double, false, 8, 4096, 512>;
+using TrN = Traits<double, false, 4, 4096, 512>;
 using L = Launcher<Tr, 3 * 256 / kDThreads, 2>;  // driver CTAs per SM: register-bound at 80 per thread
+using LN = Launcher<TrN, 3 * 256 / kDThreads, 2>;
 }  // namespace
 
-int launch_f64(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg) { return L::launch(a, cfg); }
-KernelLimits limits_f64() { return L::limits(); }
-int occupancy_f64(int which, int *bps) { return L::occ(which, bps); }
+int launch_f64(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg)
+{
+    return cfg.items == TrN::E ? LN::launch(a, cfg) : L::launch(a, cfg);
+}
+KernelLimits limits_f64()
+{
+    KernelLimits l = L::limits();
+    l.tile = TrN::T < Tr::T ? TrN::T : Tr::T;
+    l.items_wide = Tr::E;
+    l.items_narrow = TrN::E;
+    return l;
+}
+int occupancy_f64(int which, int *bps) { return which == 2 ? LN::occ(0, bps) : L::occ(which, bps); }
 int learned_f64(const Args<Tr::K, Tr::V> &a, const LearnedCall &lc, LaunchCfg &cfg) { return L::learned(a, lc, cfg); }
 
 }  // namespace qs

@@ -176,3 +176,50 @@ def test_capacity_overflow_reported_and_recovers():
     finally:
         qs.set_option("task_cap", 0)
     assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+
+
+@pytest.mark.parametrize("kind,items", [("i32", 16), ("f64", 8), ("kv", 8)])
+def test_narrow_tile_variant(kind, items):
+    """The narrow partition tile (QS_OPT_DRIVER_ITEMS) gives the same results:
+    sorts of several sizes and distributions, and a partition."""
+    import torch
+
+    import oracle
+
+    qs = qs_gpu()
+    qs.set_option("driver_items", items)
+    try:
+        for n, seed in ((8193, 1), (300_001, 2), ((1 << 20) + 7, 3)):
+            if kind == "i32":
+                for x in (synth.uniform_i32(n, seed), synth.mod_i32(n, seed, 1000)):
+                    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+            elif kind == "f64":
+                for dist in ("uniform", "few", "reverse"):
+                    x = synth.f64_config(dist, n, seed)
+                    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+            else:
+                k, v = synth.kv_config("mod1000", n, seed)
+                gk, gv = _sort_dev(qs, k, v)
+                ok, ov = oracle_sort(k, v)
+                assert_kv_sorted_equal(k, v, gk, gv, ok, ov)
+        n = (1 << 20) + 5
+        x = synth.uniform_f64(n, 9) if kind == "f64" else synth.uniform_i32(n, 9)
+        pivot = x[n // 3]
+        if kind == "kv":
+            v = np.arange(n, dtype=np.int32)
+            dk, dv = to_dev(x), to_dev(v)
+            split = qs.partition(dk, int(pivot), dv)
+            esplit, ek, ev = oracle.partition(x, int(pivot), v)
+            torch.cuda.synchronize()
+            assert split == esplit
+            assert_keys_equal(dk.cpu().numpy(), ek)
+            np.testing.assert_array_equal(dv.cpu().numpy(), ev)
+        else:
+            d = to_dev(x)
+            split = qs.partition(d, pivot)
+            esplit, ek = oracle.partition(x, pivot)
+            torch.cuda.synchronize()
+            assert split == esplit
+            assert_keys_equal(d.cpu().numpy(), ek)
+    finally:
+        qs.set_option("driver_items", 0)
