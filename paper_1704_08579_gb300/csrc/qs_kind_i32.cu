@@ -8,8 +8,11 @@ namespace {
 // the narrow one is chosen per call by QS_OPT_DRIVER_ITEMS (the autotuner).
 using Tr = Traits<int32_t, false, 8, 8192, 512>;
 using TrN = Traits<int32_t, false, 4, 8192, 512>;
-using L = Launcher<Tr, 3 * 256 / kDThreads, 2>;  // driver CTAs per SM: register-bound at 80 per thread
-using LN = Launcher<TrN, 3 * 256 / kDThreads, 2>;
+// Minimum CTAs per SM: driver 3 (80 registers per thread), leaf 4 (64
+// registers; the compare-exchange network is ALU-bound and hides its few
+// spills; measured faster than 2 or 3 for every kind).
+using L = Launcher<Tr, 3 * 256 / kDThreads, 4>;
+using LN = Launcher<TrN, 3 * 256 / kDThreads, 4>;
 }  // namespace
 
 int launch_i32(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg)
