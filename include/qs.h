@@ -246,21 +246,25 @@ typedef struct {
     double ms_leaf;         /* device time of the leaf kernel (profiling on) */
     double ms_copy;         /* device time of the partition copy-back (profiling on) */
     double ms_total;        /* device time of the whole call (profiling on) */
-    /* Profiling on: SM clock cycles the persistent kernel's CTAs spent, summed
+    /* QS_OPT_PROFILE = 2: SM clock cycles the persistent kernel's CTAs spent, summed
      * over CTAs, in [0] waiting for work, [1] waiting for a tile's keys,
      * [2] comparing and counting, [3] the look-back, [4] staging and storing,
      * [5] releasing the tile, [6] completing tasks (pivots, children);
      * [7] = tiles processed; [8] cycles inside the look-back proper (warp 0),
      * [9] cycles the middle warps waited for the prefetched tile, [10] look-back
-     * windows of 32 words read, [11] re-reads of unpublished words;
+     * windows of 32 words read, [11] re-reads of unpublished words (ordered
+     * placement; unordered: [9] the release fence, [10] the release atomic,
+     * [11] issuing the ticket claim);
      * [13] claiming and resolving the next ticket and issuing its load
      * (thread 0); [12], [14], [15] look-back phase as seen by the counting
      * warps, warp 0 and the last warp; [16] staging (warp 0), [17] staging
      * (last warp), [18] the count phase's compare-and-ballot work (thread 0);
      * leaf kernel: [19] packing parts into thread groups (thread 0), per
      * group [20] loading, [21] the network, [23] storing, and [22] padding
-     * slots sorted. */
-    int64_t driver_cycles[24];
+     * slots sorted; [24] resolving the next ticket, [25] issuing its load
+     * (thread 0); [26] sampling the children's pivots, [27] allocating them,
+     * [28] publishing their tickets (task completion). */
+    int64_t driver_cycles[32];
     int64_t bucket_max;     /* learned / bucket pass: largest bucket */
     int64_t bucket_over;    /* learned / bucket pass: buckets above 4x their even share */
     int64_t bucket_dev;     /* learned / bucket pass: sum over the B buckets of |size * B - n|;
@@ -272,8 +276,11 @@ int qs_get_stats(qs_stats *out);
 
 /*
  * Options (process-wide).  Returns QS_OK or QS_ERR_INVALID_ARG.
- *   QS_OPT_PROFILE       0/1: record CUDA events around each kernel of a
- *                        call, on the call's stream (fills ms_* in qs_stats).
+ *   QS_OPT_PROFILE       1: record CUDA events around each kernel of a
+ *                        call, on the call's stream (fills ms_* in qs_stats);
+ *                        2: also count SM cycles per phase inside the
+ *                        kernels (fills driver_cycles; the counting itself
+ *                        slows the kernels a little); 0: off.
  *   QS_OPT_WAIT_LIMIT_NS limit of every device-side wait (default 2e9 ns);
  *                        a wait that runs out ends the kernel with
  *                        QS_ERR_TIMEOUT instead of hanging.
@@ -292,6 +299,14 @@ int qs_get_stats(qs_stats *out);
  *                        32 / 16, f64 16 / 8, kv 16 / 8); the narrow value
  *                        selects the narrow one, any other value (0 included)
  *                        the wide one.
+ *   QS_OPT_ORDERED       0 (default): inside a sort, each partition tile
+ *                        claims its lower- and upper-side output ranges with
+ *                        one atomic add each on its task's two counters, so
+ *                        tiles land in claim order; 1: tiles are placed in
+ *                        input order by the decoupled look-back, as in
+ *                        qs_partition_* (which always does so).  The sorted
+ *                        keys are the same either way; with key/value pairs
+ *                        the order of the values of equal keys may differ.
  * The tuning options are what the autotuner (paper_1704_08579_gb300.autotune)
  * searches.
  */
@@ -302,7 +317,8 @@ enum {
     QS_OPT_DRIVER_CTAS = 4,
     QS_OPT_LEAF_MAX = 5,
     QS_OPT_SMALL_MAX = 6,
-    QS_OPT_DRIVER_ITEMS = 7
+    QS_OPT_DRIVER_ITEMS = 7,
+    QS_OPT_ORDERED = 8
 };
 int qs_set_option(int option, int64_t value);
 

@@ -31,7 +31,7 @@ STATUS = {
 }
 KIND = {"i32": 0, "f64": 1, "kv": 2}
 OPTION = {"profile": 1, "wait_limit_ns": 2, "task_cap": 3, "driver_ctas": 4, "leaf_max": 5, "small_max": 6,
-          "driver_items": 7}
+          "driver_items": 7, "ordered": 8}
 
 _lib = None
 _lock = threading.Lock()
@@ -48,7 +48,7 @@ class Stats(ctypes.Structure):
         "n", "kind", "part_tasks", "part_keys", "leaf_parts", "leaf_keys", "copy_keys", "max_depth",
         "lookback_words", "grid_driver", "grid_leaf")] + [
         (name, ctypes.c_double) for name in ("ms_driver", "ms_leaf", "ms_copy", "ms_total")] + [
-        ("driver_cycles", ctypes.c_int64 * 24), ("bucket_max", ctypes.c_int64), ("bucket_over", ctypes.c_int64),
+        ("driver_cycles", ctypes.c_int64 * 32), ("bucket_max", ctypes.c_int64), ("bucket_over", ctypes.c_int64),
         ("bucket_dev", ctypes.c_int64)]
 
 

@@ -21,13 +21,14 @@ namespace {
 thread_local std::string t_error;
 thread_local qs_stats t_stats;
 
-std::atomic<int> g_profile{0};
+std::atomic<int> g_profile{0};  // 1: CUDA events around kernels; 2: also in-kernel cycle counters
 std::atomic<int64_t> g_wait_limit_ns{2000000000ll};
 std::atomic<int64_t> g_task_cap{0};
 std::atomic<int64_t> g_driver_ctas{0};
 std::atomic<int64_t> g_leaf_max{0};   // 0 = the kind's compiled maximum
 std::atomic<int64_t> g_small_max{0};  // 0 = the kind's compiled maximum
 std::atomic<int64_t> g_driver_items{0};  // 0 = the wide partition tile
+std::atomic<int> g_ordered{0};  // 1 = the sort's partitions place tiles in input order too
 
 constexpr int64_t kMaxN = 1ll << 38;
 
@@ -301,7 +302,8 @@ Args<K, int32_t> make_args(Workspace &w, int kind, K *keys, int32_t *vals, int64
     a.leaf_max = leaf_max_of(kind);
     a.small_max = small_max_of(kind);
     a.wait_limit_ns = static_cast<uint64_t>(g_wait_limit_ns.load());
-    a.profile = g_profile.load();
+    a.ordered = g_ordered.load();
+    a.profile = g_profile.load() >= 2 ? 1 : 0;
     return a;
 }
 
@@ -369,7 +371,8 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     a.wait_limit_ns = static_cast<uint64_t>(g_wait_limit_ns.load());
     a.pivot_bits = pivot_bits;
     a.partition_only = partition_only;
-    a.profile = g_profile.load();
+    a.ordered = partition_only ? 1 : g_ordered.load();
+    a.profile = g_profile.load() >= 2 ? 1 : 0;
     a.seg_off = seg_off;
     a.nseg = nseg;
     (void)lim;
@@ -401,9 +404,10 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
         // kernel, leaf kernel, status read-back) per argument set.
         cfg.profile = 0;
         char key[320];
-        snprintf(key, sizeof(key), "%d:%p:%p:%p:%lld:%lld:%lld:%lld:%d:%d:%d:%llu", kind, (void *)keys, (void *)vals,
-                 (const void *)seg_off, (long long)n, (long long)nseg, (long long)a.leaf_max, (long long)a.small_max,
-                 cfg.grid_driver, cfg.grid_leaf, cfg.items, (unsigned long long)a.wait_limit_ns);
+        snprintf(key, sizeof(key), "%d:%p:%p:%p:%lld:%lld:%lld:%lld:%d:%d:%d:%d:%llu", kind, (void *)keys,
+                 (void *)vals, (const void *)seg_off, (long long)n, (long long)nseg, (long long)a.leaf_max,
+                 (long long)a.small_max, cfg.grid_driver, cfg.grid_leaf, cfg.items, a.ordered,
+                 (unsigned long long)a.wait_limit_ns);
         cudaGraphExec_t exec = nullptr;
         for (auto &g : w.graphs)
             if (g.key == key) exec = g.exec;
@@ -839,7 +843,8 @@ int qs_set_option(int option, int64_t value)
 {
     switch (option) {
     case QS_OPT_PROFILE:
-        g_profile = value ? 1 : 0;
+        if (value < 0 || value > 2) return QS_ERR_INVALID_ARG;
+        g_profile = static_cast<int>(value);
         return QS_OK;
     case QS_OPT_WAIT_LIMIT_NS:
         if (value < 0) return QS_ERR_INVALID_ARG;
@@ -856,6 +861,10 @@ int qs_set_option(int option, int64_t value)
     case QS_OPT_DRIVER_ITEMS:
         if (value < 0 || value > 64) return QS_ERR_INVALID_ARG;
         g_driver_items = value;
+        return QS_OK;
+    case QS_OPT_ORDERED:
+        if (value < 0 || value > 1) return QS_ERR_INVALID_ARG;
+        g_ordered = static_cast<int>(value);
         return QS_OK;
     case QS_OPT_LEAF_MAX:
     case QS_OPT_SMALL_MAX:

@@ -163,12 +163,22 @@ __device__ __forceinline__ long long ld_relaxed_s64(const long long *p)
 // Fetch-and-add with release (this thread's earlier writes, and the writes it
 // has observed through a CTA barrier, become visible first) and acquire (the
 // writes released by earlier adders become visible to this thread).
-__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long *p, unsigned long long v)
+__device__ __forceinline__ unsigned long long atom_add_relaxed_u64(unsigned long long *p, unsigned long long v)
 {
     unsigned long long old;
-    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    asm volatile("atom.relaxed.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
     return old;
 }
+// SM cycle counter for the profiling slots.  The asm statement is volatile
+// with a memory clobber so the compiler keeps it between the barriers and
+// memory operations it is meant to bracket.
+__device__ __forceinline__ long long prof_clock()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%clock64;" : "=l"(t)::"memory");
+    return t;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;
@@ -184,6 +194,7 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
 __device__ __forceinline__ void mbar_init(unsigned long long *bar, int count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");

@@ -13,18 +13,25 @@
 // shared memory with a 1-D TMA bulk copy, so loads overlap the scan, the
 // look-back and the stores.
 //
-// Partition order inside a task (fixed so the result is deterministic): keys
-// going to the lower side keep input order; keys going to the upper side are
-// written from the end of the range backwards, i.e. in reverse input order --
-// what one pass with a left write cursor and a right write cursor produces
-// (the paper's left_w / right_w).
+// Placement of a tile's keys.  Ordered (qs_partition_*, and sorts with
+// QS_OPT_ORDERED): fixed so the result is deterministic -- keys going to the
+// lower side keep input order; keys going to the upper side are written from
+// the end of the range backwards, i.e. in reverse input order -- what one
+// pass with a left write cursor and a right write cursor produces (the
+// paper's left_w / right_w); a tile learns how many keys of each side come
+// before it from the decoupled look-back.  Unordered (the sort's default): a
+// tile claims its lower-side range from the front and its upper-side range
+// from the back with one atomic add each on the task's two counters, so
+// tiles land in claim order and no tile waits for another; inside a tile the
+// order is the ordered one.  Either way the lower side holds exactly the
+// keys below the pivot, which is all the recursion needs.
 //
-// Every written tile is released (its stores ordered before an acq_rel add on
-// the task's tile counter); the CTA whose release is the task's last, in
-// whatever order the tiles finish, completes the task without waiting for
-// anyone: it picks the pivots of the children (median of 64 sampled keys) and
-// queues them, or lists them for the Bitonic kernel when they hold at most
-// leaf_max keys.
+// Every written tile is released (its stores ordered by a gpu-scope fence
+// before an add on the task's tile counter); the CTA whose release is the
+// task's last, in whatever order the tiles finish, completes the task without
+// waiting for anyone: it picks the pivots of the children (median of 64
+// sampled keys) and queues them, or lists them for the Bitonic kernel when
+// they hold at most leaf_max keys.
 #pragma once
 
 #include "qs_bitonic.cuh"
@@ -35,8 +42,12 @@ namespace qs {
 // ---------------------------------------------------------------------------
 // Pivot selection.  The paper's experiments use a median of three values
 // (Section IV-A); here the median of 64 keys sampled at jittered strides over
-// the range, sorted by one warp with the Bitonic network.  Called by a full
-// warp; returns the pivot's raw bits (int32 sign-extended, or IEEE bits).
+// the range: element 32 of the 64 in sorted order.  It is found by rank, not
+// by sorting: every lane counts, for its two samples, the samples below and
+// not above them, reading all 64 with independent shuffles -- a sort would be
+// a chain of ~20 dependent shuffle stages, each queued behind the other
+// CTAs' shared-memory traffic.  Called by a full warp; returns the pivot's
+// raw bits (int32 sign-extended, or IEEE bits).
 // ---------------------------------------------------------------------------
 template <class K>
 __device__ uint64_t sample_median(const K *src, int64_t off, int64_t len, uint64_t salt)
@@ -53,8 +64,25 @@ __device__ uint64_t sample_median(const K *src, int64_t off, int64_t len, uint64
         const int64_t jitter = static_cast<int64_t>(h % static_cast<uint64_t>(stride > 0 ? stride : 1));
         s[r] = Ops::to_s(__ldcg(src + off + (static_cast<int64_t>(i) * len) / 64 + jitter));
     }
-    warp_bitonic_sort<2, S>(s);
-    return Ops::to_bits(Ops::from_s(__shfl_sync(0xffffffffu, s[0], 16)));  // element 32 of 64, raw bits
+    int lt[2] = {0, 0}, le[2] = {0, 0};
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+        const S o0 = __shfl_sync(0xffffffffu, s[0], j);
+        const S o1 = __shfl_sync(0xffffffffu, s[1], j);
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            lt[r] += (o0 < s[r] ? 1 : 0) + (o1 < s[r] ? 1 : 0);
+            le[r] += (o0 <= s[r] ? 1 : 0) + (o1 <= s[r] ? 1 : 0);
+        }
+    }
+    // Element 32 of the sorted samples is a sample x with lt(x) <= 32 < le(x).
+    const bool h0 = lt[0] <= 32 && 32 < le[0];
+    const bool h1 = lt[1] <= 32 && 32 < le[1];
+    const unsigned m0 = __ballot_sync(0xffffffffu, h0);
+    const unsigned m1 = __ballot_sync(0xffffffffu, h1);
+    const int from = m0 ? __ffs(m0) - 1 : __ffs(m1) - 1;
+    const S x = __shfl_sync(0xffffffffu, h0 ? s[0] : s[1], from);
+    return Ops::to_bits(Ops::from_s(x));
 }
 
 // ---------------------------------------------------------------------------
@@ -103,6 +131,7 @@ __device__ bool alloc_task(const Args<typename Tr::K, typename Tr::V> &a, int64_
     t->tiles_done = 0;
     t->eq = 0;
     t->lt_total = 0;
+    t->hi_total = 0;
     __threadfence();
     atomicAdd(&c->part_tasks, 1ull);
     atomicAdd(&c->part_keys, static_cast<unsigned long long>(len));
@@ -114,8 +143,9 @@ __device__ bool alloc_task(const Args<typename Tr::K, typename Tr::V> &a, int64_
 }
 
 // Thread 0: allocates the partition children of a finished task (want[i])
-// with one atomic on the task count and one on the ticket cursor, writes
-// their fields and orders them before any later store of this CTA.
+// with one atomic on the task count and one on the ticket cursor and writes
+// their fields; the fences of publish_task(), after a CTA barrier, order
+// these writes before the tickets become claimable.
 template <class Tr>
 __device__ void alloc_children(const Args<typename Tr::K, typename Tr::V> &a, const bool (&want)[2],
                                const int64_t (&off)[2], const int64_t (&len)[2], int src, const uint64_t (&pivot)[2],
@@ -162,6 +192,7 @@ __device__ void alloc_children(const Args<typename Tr::K, typename Tr::V> &a, co
         t->tiles_done = 0;
         t->eq = 0;
         t->lt_total = 0;
+        t->hi_total = 0;
         nt[i].id = static_cast<long long>(nid);
         nt[i].g0 = static_cast<long long>(ng);
         nt[i].ntiles = nti[i];
@@ -170,7 +201,6 @@ __device__ void alloc_children(const Args<typename Tr::K, typename Tr::V> &a, co
         ++nid;
         ng += static_cast<unsigned long long>(nti[i]);
     }
-    __threadfence();
     atomicAdd(&c->part_tasks, static_cast<unsigned long long>(cnt));
     atomicAdd(&c->part_keys, keys);
     atomicMax(&c->max_depth, static_cast<unsigned long long>(depth));
@@ -248,6 +278,7 @@ struct DriverSmem {
     alignas(8) unsigned long long bar[2];
     int wcount[Tr::VPT * kDWarps];
     long long excl;
+    long long hexcl;  // unordered placement: upper-side keys placed before this tile
     long long first;
     int low_total;
     int eq_total;
@@ -505,11 +536,22 @@ __device__ __forceinline__ void release_prev(const Args<typename Tr::K, typename
     if (sm.has_prev) {
         Task *t = a.tasks + sm.wp.task;
         if (sm.prev_eq) atomicAdd(&t->eq, static_cast<unsigned long long>(sm.prev_eq));
-        // acq_rel: releases the tile's stores (and lt_total, eq); the last
-        // adder acquires every other tile's.
-        const unsigned long long done = atom_add_acq_rel_u64(&t->tiles_done, 1ull);
+        // The fence releases the tile's stores (and its counts); the last
+        // adder's second fence acquires every other tile's.
+        const long long t0 = a.profile ? prof_clock() : 0;
+        fence_acq_rel_gpu();
+        const long long t1 = a.profile ? prof_clock() : 0;
+        const unsigned long long done = atom_add_relaxed_u64(&t->tiles_done, 1ull);
         last = done == static_cast<unsigned long long>(sm.wp.ntiles - 1) ? 1 : 0;
-        if (last) sm.wf = sm.wp;
+        if (a.profile && !a.ordered) {
+            const long long t2 = prof_clock();
+            sm.tm[9] += t1 - t0;
+            sm.tm[10] += t2 - t1;
+        }
+        if (last) {
+            fence_acq_rel_gpu();
+            sm.wf = sm.wp;
+        }
         sm.has_prev = 0;
     }
     sm.prev_last = last;
@@ -543,12 +585,25 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     const int64_t off = w.off, end = w.off + w.len;
     const int64_t base = w.w0 + static_cast<int64_t>(w.tile) * T;
 
-    long long tprev = (a.profile && tid == 0) ? clock64() : 0;
+    long long tprev = (a.profile && tid == 0) ? prof_clock() : 0;
 #define QS_TICK(slot)                         \
     if (a.profile && tid == 0) {              \
-        const long long tnow_ = clock64();    \
+        const long long tnow_ = prof_clock();    \
         sm.tm[slot] += tnow_ - tprev;         \
         tprev = tnow_;                        \
+    }
+
+    // Unordered placement: the last warp releases the previous tile first;
+    // its fence waits for this SM's earlier stores to drain while the other
+    // warps compare.  (Ordered placement releases in the look-back phase,
+    // where the middle warps count the next tile meanwhile.)
+    if (!a.ordered && warp == kDWarps - 1) {
+        if (lane == 0) {
+            const long long trl = a.profile ? prof_clock() : 0;
+            release_prev<Tr>(a, sm);
+            if (a.profile) sm.tm[5] += prof_clock() - trl;
+        }
+        __syncwarp();
     }
 
     K key[E];
@@ -610,10 +665,10 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) eq += __shfl_xor_sync(0xffffffffu, eq, o);
     if (lane == 0 && eq) atomicAdd(&sm.eq_total, eq);
-    if (a.profile && tid == 0) sm.tm[18] += clock64() - tprev;  // own work, before the barrier
+    if (a.profile && tid == 0) sm.tm[18] += prof_clock() - tprev;  // own work, before the barrier
     __syncthreads();
     QS_TICK(2);
-    const long long tph = a.profile ? clock64() : 0;  // start of the look-back phase
+    const long long tph = a.profile ? prof_clock() : 0;  // start of the look-back phase
 
     // Staging in output order (lower-side keys at [0, L), upper-side keys
     // after them) depends only on this tile's own counts, not on the global
@@ -670,36 +725,62 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         if (lane == 0) sm.low_total = total;
         __syncwarp();
         asm volatile("bar.arrive 2, %0;" ::"n"(kDThreads) : "memory");
-        const long long tlb = a.profile ? clock64() : 0;
-        int nwin, nspin;
-        const long long excl = lookback(a.pool + w.pool, w.tile, static_cast<unsigned long long>(total), a.ctrl,
-                                        a.wait_limit_ns, w.a_pub != 0, nwin, nspin);
-        if (a.profile && lane == 0) {
-            sm.tm[8] += clock64() - tlb;
-            sm.tm[10] += nwin;
-            sm.tm[11] += nspin;
-        }
-        if (lane == 0) {
-            sm.excl = excl;
-            sm.abort = excl < 0;
-            if (excl >= 0 && w.tile == w.ntiles - 1)
-                st_relaxed_u64(&a.tasks[w.task].lt_total, static_cast<unsigned long long>(excl + total));
-        }
-        const long long tst = a.profile ? clock64() : 0;
-        stage(total);
-        if (a.profile && lane == 0) {
-            const long long now = clock64();
-            sm.tm[16] += now - tst;
-            sm.tm[14] += now - tph;
+        const long long tlb = a.profile ? prof_clock() : 0;
+        if (a.ordered) {
+            int nwin, nspin;
+            const long long excl = lookback(a.pool + w.pool, w.tile, static_cast<unsigned long long>(total), a.ctrl,
+                                            a.wait_limit_ns, w.a_pub != 0, nwin, nspin);
+            if (a.profile && lane == 0) {
+                sm.tm[8] += prof_clock() - tlb;
+                sm.tm[10] += nwin;
+                sm.tm[11] += nspin;
+            }
+            if (lane == 0) {
+                sm.excl = excl;
+                sm.abort = excl < 0;
+                if (excl >= 0 && w.tile == w.ntiles - 1)
+                    st_relaxed_u64(&a.tasks[w.task].lt_total, static_cast<unsigned long long>(excl + total));
+            }
+            const long long tst = a.profile ? prof_clock() : 0;
+            stage(total);
+            if (a.profile && lane == 0) {
+                const long long now = prof_clock();
+                sm.tm[16] += now - tst;
+                sm.tm[14] += now - tph;
+            }
+        } else {
+            // Unordered placement: lane 0 claims the tile's lower-side range
+            // and lane 1 its upper-side range on the task's two counters; the
+            // replies arrive while the warp stages its keys.
+            Task *t = a.tasks + w.task;
+            const unsigned long long cnt =
+                static_cast<unsigned long long>(lane == 0 ? total : nvalid - total);
+            unsigned long long got = 0;
+            if (lane < 2 && cnt) got = atomicAdd(lane == 0 ? &t->lt_total : &t->hi_total, cnt);
+            const long long tst = a.profile ? prof_clock() : 0;
+            stage(total);
+            const long long excl = static_cast<long long>(__shfl_sync(0xffffffffu, got, 0));
+            const long long hexcl = static_cast<long long>(__shfl_sync(0xffffffffu, got, 1));
+            if (lane == 0) {
+                sm.excl = excl;
+                sm.hexcl = hexcl;
+                sm.abort = 0;
+            }
+            if (a.profile && lane == 0) {
+                const long long now = prof_clock();
+                sm.tm[8] += now - tlb;
+                sm.tm[16] += now - tst;
+                sm.tm[14] += now - tph;
+            }
         }
     } else if (warp < kDWarps - 1) {
-        if (nx.kind == 1 && nx.full && !nx.a_pub) {
+        if (a.ordered && nx.kind == 1 && nx.full && !nx.a_pub) {
             // The middle warps first count the prefetched next tile and
             // publish its aggregate, so tiles after it never wait for this CTA
             // to finish the current tile.
-            const long long tmb = (a.profile && tid == 32) ? clock64() : 0;
+            const long long tmb = (a.profile && tid == 32) ? prof_clock() : 0;
             const bool landed = mbar_wait_bounded(&sm.bar[b ^ 1], (phases >> (b ^ 1)) & 1u, a.ctrl, a.wait_limit_ns);
-            if (a.profile && tid == 32) sm.tm[9] += clock64() - tmb;
+            if (a.profile && tid == 32) sm.tm[9] += prof_clock() - tmb;
             if (landed) {
                 int cnt = count_low_any<Tr>(sm.kbuf[b ^ 1], nx.pivot, nx.mode);
 #pragma unroll
@@ -716,21 +797,21 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         }
         asm volatile("bar.sync 2, %0;" ::"n"(kDThreads) : "memory");  // chunk offsets are ready
         stage(sm.low_total);
-        if (a.profile && tid == 32) sm.tm[12] += clock64() - tph;
+        if (a.profile && tid == 32) sm.tm[12] += prof_clock() - tph;
     } else {
-        // The last warp releases the previous tile meanwhile: its fence waits
-        // for this SM's earlier stores to drain, off the other warps' path.
-        if (lane == 0) {
-            const long long trl = a.profile ? clock64() : 0;
-            release_prev<Tr>(a, sm);
-            if (a.profile) sm.tm[5] += clock64() - trl;
+        if (a.ordered) {
+            if (lane == 0) {
+                const long long trl = a.profile ? prof_clock() : 0;
+                release_prev<Tr>(a, sm);
+                if (a.profile) sm.tm[5] += prof_clock() - trl;
+            }
+            __syncwarp();
         }
-        __syncwarp();
         asm volatile("bar.sync 2, %0;" ::"n"(kDThreads) : "memory");  // chunk offsets are ready
-        const long long tst = a.profile ? clock64() : 0;
+        const long long tst = a.profile ? prof_clock() : 0;
         stage(sm.low_total);
         if (a.profile && lane == 0) {
-            const long long now = clock64();
+            const long long now = prof_clock();
             sm.tm[17] += now - tst;
             sm.tm[15] += now - tph;
         }
@@ -742,8 +823,9 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     const long long excl = sm.excl;
 
     // Lower side: [off + excl, +L); upper side (reverse order) ends at
-    // end - 1 - hpre, where hpre = upper-side keys of the earlier tiles.
-    const int64_t hpre = (vstart - off) - excl;
+    // end - 1 - hpre, where hpre = upper-side keys placed before this tile
+    // (ordered: those of the earlier tiles).
+    const int64_t hpre = a.ordered ? (vstart - off) - excl : sm.hexcl;
     const int H = nvalid - L;
     if (excl >= 0 && off + excl + L <= end && hpre >= 0 && hpre + H <= w.len) {
         K *__restrict__ lo_k = a.keys[w.src ^ 1] + (off + excl);
@@ -830,6 +912,7 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
     // Children that are partition tasks: their pivots (warp i samples child
     // i), then thread 0 allocates both, then the whole CTA publishes their
     // tickets.
+    long long tf = (a.profile && tid == 0) ? prof_clock() : 0;
     const int wi = tid >> 5;
     if (wi < 2) {
         uint64_t pb = w.pivot;
@@ -840,6 +923,11 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
     }
     __syncthreads();
     if (tid == 0) {
+        if (a.profile) {
+            const long long now = prof_clock();
+            sm.tm[26] += now - tf;
+            tf = now;
+        }
         bool want[2];
         int64_t coff[2], clen[2];
         uint64_t piv[2];
@@ -855,10 +943,16 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
         }
         alloc_children<Tr>(a, want, coff, clen, dst, piv, mode, __ldcg(&t->depth) + 1, sm.nt, sm.nt_ok);
         sm.low_total = sm.nt_ok[0] + sm.nt_ok[1];
+        if (a.profile) {
+            const long long now = prof_clock();
+            sm.tm[27] += now - tf;
+            tf = now;
+        }
     }
     __syncthreads();
     for (int i = 0; i < 2; ++i)
         if (sm.nt_ok[i]) publish_task(a.owner, sm.nt[i], -1, kDThreads);
+    if (a.profile && tid == 0) sm.tm[28] += prof_clock() - tf;
     for (int i = 0; i < 2; ++i) {
         // Finished run of equal keys: copy back only if it sits in scratch.
         if (sm.c_kind[i] != 1 || dst != 1) continue;
@@ -899,9 +993,9 @@ __device__ void flush_release(const Args<typename Tr::K, typename Tr::V> &a, Dri
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const long long trl = a.profile ? clock64() : 0;
+        const long long trl = a.profile ? prof_clock() : 0;
         release_prev<Tr>(a, sm);
-        if (a.profile) sm.tm[5] += clock64() - trl;
+        if (a.profile) sm.tm[5] += prof_clock() - trl;
     }
     __syncthreads();
     if (sm.prev_last) finish_task<Tr>(a, sm.wf, sm);
@@ -918,7 +1012,11 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
     const int tid = threadIdx.x;
     uint32_t phases = 0;   // bit b: parity of the next completion of bar[b]
     uint32_t pending = 0;  // bit b: a bulk load into buffer b is issued and not yet consumed
-    long long t_wait = a.profile ? clock64() : 0;
+    long long t_wait = a.profile ? prof_clock() : 0;
+    // Unordered placement: thread 0 claims each ticket one tile early, so the
+    // claim's round trip is hidden behind a whole tile.  (With ordered
+    // placement a held ticket would delay the look-back of the tiles after it.)
+    long long g_ahead = 0;
     if (tid == 0) {
         for (int i = 0; i < kProfSlots; ++i) sm.tm[i] = 0;
         mbar_init(&sm.bar[0], 1);
@@ -933,9 +1031,10 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
         const long long g = static_cast<long long>(atomicAdd(&a.ctrl->ticket_head, 1ull));
         sm.w[0] = resolve_blocking<Tr>(a, g, none);
         if (sm.w[0].kind == 1) issue_tile_load<Tr>(a, sm.w[0], sm, 0);
+        if (!a.ordered) g_ahead = static_cast<long long>(atomicAdd(&a.ctrl->ticket_head, 1ull));
     }
     __syncthreads();
-    if (a.profile && tid == 0) sm.tm[0] += clock64() - t_wait;
+    if (a.profile && tid == 0) sm.tm[0] += prof_clock() - t_wait;
     int b = 0;
     if (sm.w[0].kind == 1 && sm.w[0].full) pending |= 1u;
     bool aborted = false;
@@ -943,12 +1042,26 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
     while (sm.w[0].kind == 1) {
         if (tid == 0) {
             // Claim the next ticket now; prefetch its tile if its task is known.
-            const long long th = a.profile ? clock64() : 0;
-            const long long g = static_cast<long long>(atomicAdd(&a.ctrl->ticket_head, 1ull));
+            const long long th = a.profile ? prof_clock() : 0;
+            long long g;
+            if (a.ordered) {
+                g = static_cast<long long>(atomicAdd(&a.ctrl->ticket_head, 1ull));
+            } else {
+                g = g_ahead;
+                g_ahead = static_cast<long long>(atomicAdd(&a.ctrl->ticket_head, 1ull));
+                if (a.profile) sm.tm[11] += prof_clock() - th;
+            }
             sm.next_ticket = g;
+            const long long tr = a.profile ? prof_clock() : 0;
             sm.w[1] = try_resolve<Tr>(a, g, sm.w[0]);
+            const long long ti = a.profile ? prof_clock() : 0;
             if (sm.w[1].kind == 1) issue_tile_load<Tr>(a, sm.w[1], sm, b ^ 1);
-            if (a.profile) sm.tm[13] += clock64() - th;
+            if (a.profile) {
+                const long long now = prof_clock();
+                sm.tm[13] += now - th;
+                sm.tm[24] += ti - tr;
+                sm.tm[25] += now - ti;
+            }
         }
         const int r = partition_tile<Tr>(a, sm.w[0], sm.w[1], sm, b, phases);
         pending &= ~(1u << b);
@@ -958,15 +1071,15 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
             break;
         }
         if (sm.prev_last) {
-            const long long t6 = a.profile ? clock64() : 0;
+            const long long t6 = a.profile ? prof_clock() : 0;
             finish_task<Tr>(a, sm.wf, sm);
-            if (a.profile && tid == 0) sm.tm[6] += clock64() - t6;
+            if (a.profile && tid == 0) sm.tm[6] += prof_clock() - t6;
         }
         if (sm.w[1].kind == 0) {
             // About to wait for work: release the last written tile first, as
             // the work waited for may be its task's children.
             flush_release<Tr>(a, sm);
-            const long long t0w = a.profile ? clock64() : 0;
+            const long long t0w = a.profile ? prof_clock() : 0;
             __syncthreads();
             if (tid == 0) {
                 sm.w[1] = resolve_blocking<Tr>(a, sm.next_ticket, sm.w[0]);
@@ -974,7 +1087,7 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
             }
             __syncthreads();
             if (sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);
-            if (a.profile && tid == 0) sm.tm[0] += clock64() - t0w;
+            if (a.profile && tid == 0) sm.tm[0] += prof_clock() - t0w;
         }
         __syncthreads();
         if (tid == 0) sm.w[0] = sm.w[1];

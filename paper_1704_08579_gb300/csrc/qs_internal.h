@@ -53,7 +53,9 @@ struct alignas(16) Task {
     unsigned long long next_tile;   // tile claim counter
     unsigned long long tiles_done;  // completion counter
     unsigned long long eq;          // keys equal to the pivot
-    unsigned long long lt_total;    // keys sent to the lower side (written by the last tile)
+    unsigned long long lt_total;    // keys sent to the lower side (ordered: written by the last tile;
+                                    // unordered: the lower side's placement counter)
+    unsigned long long hi_total;    // unordered placement: keys sent to the upper side so far
 };
 
 struct alignas(16) Leaf {
@@ -64,7 +66,7 @@ struct alignas(16) Leaf {
 constexpr int kLeafScratch = 1;
 constexpr int kLeafFinal = 2;
 
-constexpr int kProfSlots = 24;  // driver profiling slots (qs_stats.driver_cycles)
+constexpr int kProfSlots = 32;  // driver profiling slots (qs_stats.driver_cycles)
 
 struct alignas(128) Ctrl {
     unsigned long long ticket_head;  // next ticket to hand out
@@ -99,6 +101,7 @@ struct Args {
     uint64_t wait_limit_ns;
     uint64_t pivot_bits;  // partition-only: the caller's pivot
     int partition_only;
+    int ordered;  // 1: tiles placed in input order (look-back); 0: each tile claims its ranges with atomics
     int profile;  // accumulate per-phase cycle counts into ctrl->cycles
     const int64_t *seg_off;  // segmented sort: nseg + 1 offsets into keys (nullptr otherwise)
     int64_t nseg;

@@ -101,7 +101,7 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     const typename Tr::K *gk = a.keys[src] + l.off;
     const typename Tr::V *gv = a.vals[src] + l.off;
     const int len = l.len;
-    long long t0 = (a.profile && g == 0) ? clock64() : 0;
+    long long t0 = (a.profile && g == 0) ? prof_clock() : 0;
     // Coalesced load, tail padded with the largest key: all E loads of a
     // thread are issued before the first one is used.
     {
@@ -118,7 +118,7 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     S k[E];
     lay_load<E, LE, S>(k, gs, g, 0);
     if (a.profile && g == 0) {
-        const long long t = clock64();
+        const long long t = prof_clock();
         atomicAdd(&a.ctrl->cycles[20], static_cast<unsigned long long>(t - t0));
         t0 = t;
     }
@@ -129,7 +129,7 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     default: group_bitonic_sort<E, LE, LE + 8, S>(k, gs, g, bar, nthreads); break;
     }
     if (a.profile && g == 0) {
-        const long long t = clock64();
+        const long long t = prof_clock();
         atomicAdd(&a.ctrl->cycles[21], static_cast<unsigned long long>(t - t0));
         atomicAdd(&a.ctrl->cycles[22], static_cast<unsigned long long>(P - len));  // padding slots
         t0 = t;
@@ -144,7 +144,7 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
         const int i = g + r * nthreads;
         if (i < len) LK::store(ok, ov, i, gs[padk<S>(i)]);
     }
-    if (a.profile && g == 0) atomicAdd(&a.ctrl->cycles[23], static_cast<unsigned long long>(clock64() - t0));
+    if (a.profile && g == 0) atomicAdd(&a.ctrl->cycles[23], static_cast<unsigned long long>(prof_clock() - t0));
 }
 
 template <class Tr, int E>
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
     // threads each, E keys per thread); a part that does not fit is carried
     // over to this CTA's next pass.
     for (;;) {
-        const long long tp = (a.profile && tid == 0) ? clock64() : 0;
+        const long long tp = (a.profile && tid == 0) ? prof_clock() : 0;
         if (tid == 0) {
             int ng = 0, used = 0;
             for (;;) {
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
                 if (used == kThreads) break;
             }
             sm.ngroups = ng;
-            if (a.profile) atomicAdd(&a.ctrl->cycles[19], static_cast<unsigned long long>(clock64() - tp));
+            if (a.profile) atomicAdd(&a.ctrl->cycles[19], static_cast<unsigned long long>(prof_clock() - tp));
         }
         __syncthreads();
         const int ng = sm.ngroups;

@@ -113,6 +113,7 @@ extern "C" int64_t qs_partition_i32_noalloc(int32_t *d_keys, int64_t n, int32_t 
     a.wait_limit_ns = 2000000000ull;
     a.pivot_bits = static_cast<uint64_t>(static_cast<int64_t>(pivot));
     a.partition_only = 1;
+    a.ordered = 1;
     a.profile = 0;
     LaunchCfg cfg;
     std::memset(&cfg, 0, sizeof(cfg));

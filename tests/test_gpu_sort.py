@@ -223,3 +223,30 @@ def test_narrow_tile_variant(kind, items):
             assert_keys_equal(d.cpu().numpy(), ek)
     finally:
         qs.set_option("driver_items", 0)
+
+
+@pytest.mark.parametrize("kind", ["i32", "f64", "kv"])
+def test_ordered_and_unordered_placement(kind):
+    """Both placements of a sort's partition tiles (QS_OPT_ORDERED) give the
+    oracle's keys: tiles claiming their output ranges with atomics (default)
+    and tiles placed in input order by the look-back."""
+    qs = qs_gpu()
+    try:
+        for ordered in (1, 0):
+            qs.set_option("ordered", ordered)
+            for n, seed in ((70_001, 31), ((1 << 21) + 3, 32)):
+                if kind == "i32":
+                    for x in (synth.uniform_i32(n, seed), synth.mod_i32(n, seed, 7)):
+                        assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+                elif kind == "f64":
+                    for dist in ("uniform", "sorted", "few"):
+                        x = synth.f64_config(dist, n, seed)
+                        assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+                else:
+                    for dist in ("uniform", "mod1000"):
+                        k, v = synth.kv_config(dist, n, seed)
+                        gk, gv = _sort_dev(qs, k, v)
+                        ok, ov = oracle_sort(k, v)
+                        assert_kv_sorted_equal(k, v, gk, gv, ok, ov)
+    finally:
+        qs.set_option("ordered", 0)
