@@ -20,7 +20,7 @@ CACHE_DIR = os.path.join(HERE, "tuning")
 
 LEAF_CHOICES = {"i32": (2048, 4096, 8192), "f64": (1024, 2048, 4096), "kv": (1024, 2048, 4096)}
 SMALL_CHOICES = (128, 256, 512)
-ITEMS_CHOICES = {"i32": (32, 16), "f64": (16, 8), "kv": (16, 8)}  # wide (default), narrow
+ITEMS_CHOICES = {"i32": (16, 32), "f64": (16, 8), "kv": (16, 8)}  # the kind's default first
 
 
 def _cache_path(gpu_name: str) -> str:

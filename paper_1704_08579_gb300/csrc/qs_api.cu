@@ -27,7 +27,7 @@ std::atomic<int64_t> g_task_cap{0};
 std::atomic<int64_t> g_driver_ctas{0};
 std::atomic<int64_t> g_leaf_max{0};   // 0 = the kind's compiled maximum
 std::atomic<int64_t> g_small_max{0};  // 0 = the kind's compiled maximum
-std::atomic<int64_t> g_driver_items{0};  // 0 = the wide partition tile
+std::atomic<int64_t> g_driver_items{0};  // 0 = the kind's default partition tile
 std::atomic<int> g_ordered{0};  // 1 = the sort's partitions place tiles in input order too
 
 constexpr int64_t kMaxN = 1ll << 38;
@@ -382,6 +382,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     cfg.stream = s;
     const int64_t ctas = g_driver_ctas.load();
     cfg.items = static_cast<int>(g_driver_items.load());
+    if (cfg.items == 0) cfg.items = limits_of(kind).items_default;
     cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas)
                                : w.sms * w.occ[kind][cfg.items == limits_of(kind).items_narrow ? 2 : 0];
     cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];
@@ -606,6 +607,7 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     cfg.stream = s;
     const int64_t ctas = g_driver_ctas.load();
     cfg.items = static_cast<int>(g_driver_items.load());
+    if (cfg.items == 0) cfg.items = limits_of(kind).items_default;
     cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas)
                                : w.sms * w.occ[kind][cfg.items == limits_of(kind).items_narrow ? 2 : 0];
     cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];

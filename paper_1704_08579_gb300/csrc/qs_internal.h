@@ -157,6 +157,7 @@ struct KernelLimits {
     int64_t leaf_max, small_max, tile;  // tile: the smaller of the two partition tile variants
     size_t driver_smem, leaf_smem;
     int items_wide, items_narrow;       // keys per thread of the two partition tile variants
+    int items_default;                  // the variant used when QS_OPT_DRIVER_ITEMS is 0
 };
 
 // Per-kind entry points implemented in qs_kind_{i32,f64,kv}.cu.  They enqueue

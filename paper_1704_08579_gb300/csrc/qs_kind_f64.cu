@@ -26,6 +26,7 @@ KernelLimits limits_f64()
     l.tile = TrN::T < Tr::T ? TrN::T : Tr::T;
     l.items_wide = Tr::E;
     l.items_narrow = TrN::E;
+    l.items_default = Tr::E;
     return l;
 }
 int occupancy_f64(int which, int *bps) { return which == 2 ? LN::occ(0, bps) : L::occ(which, bps); }

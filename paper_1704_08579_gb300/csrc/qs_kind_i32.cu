@@ -4,16 +4,21 @@
 namespace qs {
 
 namespace {
-// Two partition tile variants (items per thread); the wide one is the default,
-// the narrow one is chosen per call by QS_OPT_DRIVER_ITEMS (the autotuner).
+// Two partition tile variants (items per thread), chosen per call by
+// QS_OPT_DRIVER_ITEMS (the autotuner).  For int32 the narrow one is the
+// default: at 4 CTAs per SM (64 registers) it sorts 2^28 keys in 12.96 ms
+// against 13.40 ms for the wide one at 3.  (FP64 and key/value sorts are
+// faster with the wide tile: 16.1 vs 17.0 ms and 16.9 vs 17.5 ms of
+// partition passes at 2^28.)
 using Tr = Traits<int32_t, false, 8, 8192, 512>;
 using TrN = Traits<int32_t, false, 4, 8192, 512>;
-// Minimum CTAs per SM: driver 3 (80 registers per thread), leaf 4 (64
+// Minimum CTAs per SM: driver 3 (80 registers per thread; narrow tile 4 at
+// 64), leaf 4 (64
 // registers; the ALU-bound compare-exchange network hides its few spills --
 // FP64 leaf kernel at 2^28: 9.07 ms at 2 CTAs, 8.36 at 3, 7.96 at 4; int32
 // and key/value sorts equal at 3 and 4).
 using L = Launcher<Tr, 3 * 256 / kDThreads, 4>;
-using LN = Launcher<TrN, 3 * 256 / kDThreads, 4>;
+using LN = Launcher<TrN, 4, 4>;
 }  // namespace
 
 int launch_i32(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg)
@@ -26,6 +31,7 @@ KernelLimits limits_i32()
     l.tile = TrN::T < Tr::T ? TrN::T : Tr::T;
     l.items_wide = Tr::E;
     l.items_narrow = TrN::E;
+    l.items_default = TrN::E;
     return l;
 }
 int occupancy_i32(int which, int *bps) { return which == 2 ? LN::occ(0, bps) : L::occ(which, bps); }

@@ -26,6 +26,7 @@ KernelLimits limits_kv()
     l.tile = TrN::T < Tr::T ? TrN::T : Tr::T;
     l.items_wide = Tr::E;
     l.items_narrow = TrN::E;
+    l.items_default = Tr::E;
     return l;
 }
 int occupancy_kv(int which, int *bps) { return which == 2 ? LN::occ(0, bps) : L::occ(which, bps); }
