@@ -248,15 +248,17 @@ typedef struct {
     double ms_total;        /* device time of the whole call (profiling on) */
     /* QS_OPT_PROFILE = 2: SM clock cycles the persistent kernel's CTAs spent, summed
      * over CTAs, in [0] waiting for work, [1] waiting for a tile's keys,
-     * [2] comparing and counting, [3] the look-back, [4] staging and storing,
+     * [2] comparing and counting, [3] placing the tile (look-back or range
+     * claims) and staging, [4] storing,
      * [5] releasing the tile, [6] completing tasks (pivots, children);
-     * [7] = tiles processed; [8] cycles inside the look-back proper (warp 0),
+     * [7] = tiles processed; [8] cycles inside the look-back proper, or the
+     * range claims and staging of unordered placement (warp 0),
      * [9] cycles the middle warps waited for the prefetched tile, [10] look-back
      * windows of 32 words read, [11] re-reads of unpublished words (ordered
      * placement; unordered: [9] the release fence, [10] the release atomic,
      * [11] issuing the ticket claim);
      * [13] claiming and resolving the next ticket and issuing its load
-     * (thread 0); [12], [14], [15] look-back phase as seen by the counting
+     * (thread 0); [12], [14], [15] placement phase as seen by the counting
      * warps, warp 0 and the last warp; [16] staging (warp 0), [17] staging
      * (last warp), [18] the count phase's compare-and-ballot work (thread 0);
      * leaf kernel: [19] packing parts into thread groups (thread 0), per

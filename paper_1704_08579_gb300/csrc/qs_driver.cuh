@@ -562,7 +562,8 @@ __device__ __forceinline__ void release_prev(const Args<typename Tr::K, typename
 // k*NT*VW + t*VW + j, so the input order is (k, warp, lane, j).  The pivot
 // compare (the paper's vector compare into a mask) becomes warp ballots whose
 // popcounts give every key its rank among the tile's lower-side keys; a CTA
-// scan of the (k, warp) counts plus the look-back give its global position.
+// scan of the (k, warp) counts plus the look-back (ordered placement) or the
+// tile's two range claims (unordered) give its global position.
 // Keys are staged in shared memory in output order and written with
 // coalesced stores.  Returns 0, or -1 on abort.  On return sm.prev_last says
 // whether the deferred release of the previous tile completed its task
@@ -668,13 +669,13 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     if (a.profile && tid == 0) sm.tm[18] += prof_clock() - tprev;  // own work, before the barrier
     __syncthreads();
     QS_TICK(2);
-    const long long tph = a.profile ? prof_clock() : 0;  // start of the look-back phase
+    const long long tph = a.profile ? prof_clock() : 0;  // start of the placement phase
 
     // Staging in output order (lower-side keys at [0, L), upper-side keys
     // after them) depends only on this tile's own counts, not on the global
     // offset; so warp 0 scans the chunk counts and releases the other warps
-    // (named barrier 2) before it starts the look-back, and they stage their
-    // keys meanwhile.
+    // (named barrier 2) before it starts the look-back or the range claims,
+    // and they stage their keys meanwhile.
     const int64_t vstart = base > off ? base : off;
     const int64_t vend = base + T < end ? base + T : end;
     const int nvalid = static_cast<int>(vend - vstart);

@@ -29,6 +29,44 @@ def test_version_and_options(lib):
     assert lib.qs_set_option(qs.OPTION["profile"], 0) == 0
 
 
+def test_option_value_ranges(lib):
+    """Every option's documented range (include/qs.h); an out-of-range value
+    returns QS_ERR_INVALID_ARG and leaves the option alone."""
+    opt = qs.OPTION
+    for v in (0, 1, 2):
+        assert lib.qs_set_option(opt["profile"], v) == 0
+    for v in (-1, 3):
+        assert lib.qs_set_option(opt["profile"], v) == -1
+    for v in (0, 1):
+        assert lib.qs_set_option(opt["ordered"], v) == 0
+    for v in (-1, 2):
+        assert lib.qs_set_option(opt["ordered"], v) == -1
+    for v in (0, 8, 16, 32):
+        assert lib.qs_set_option(opt["driver_items"], v) == 0
+    for v in (-1, 65):
+        assert lib.qs_set_option(opt["driver_items"], v) == -1
+    for name in ("leaf_max", "small_max"):
+        for v in (0, 32, 512, 4096):
+            assert lib.qs_set_option(opt[name], v) == 0
+        for v in (-1, 16, 48, 1000):
+            assert lib.qs_set_option(opt[name], v) == -1
+    assert lib.qs_set_option(opt["driver_ctas"], -1) == -1
+    assert lib.qs_set_option(opt["driver_ctas"], (1 << 20) + 1) == -1
+    assert lib.qs_set_option(opt["task_cap"], -1) == -1
+    for name in ("profile", "ordered", "driver_items", "leaf_max", "small_max", "driver_ctas", "task_cap"):
+        assert lib.qs_set_option(opt[name], 0) == 0
+    assert lib.qs_set_option(opt["wait_limit_ns"], 2_000_000_000) == 0
+
+
+def test_option_names_match_header():
+    """The binding's option numbers are the header's QS_OPT_* values."""
+    import re
+
+    text = open(qs.HEADER).read()
+    found = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"QS_OPT_([A-Z_]+)\s*=\s*(\d+)", text)}
+    assert found == qs.OPTION
+
+
 def test_host_argument_checks(lib):
     null = ctypes.c_void_p(0)
     assert lib.qs_sort_i32(null, 0, null) == 0          # n == 0 is a no-op
