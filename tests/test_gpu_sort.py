@@ -252,3 +252,37 @@ def test_ordered_and_unordered_placement(kind):
                         assert_kv_sorted_equal(k, v, gk, gv, ok, ov)
     finally:
         qs.set_option("ordered", 0)
+
+
+@pytest.mark.parametrize("kind", ["i32", "f64", "kv"])
+def test_small_leaf_thresholds(kind):
+    """Run-time leaf / one-warp thresholds down to the minimum (32): the
+    recursion then reaches partition tasks of 33 keys, whose tiles are
+    nearly all ragged edges, and deep trees of tiny tasks -- with both tile
+    placements.  Keys against the oracle (key/value: value multisets per run
+    of equal keys)."""
+    qs = qs_gpu()
+    try:
+        for leaf, small in ((32, 32), (64, 32), (512, 64), (2048, 256)):
+            qs.set_option("leaf_max", leaf)
+            qs.set_option("small_max", small)
+            for ordered in (0, 1):
+                qs.set_option("ordered", ordered)
+                for n, seed in ((30_011, 41), (200_003, 42)):
+                    if kind == "i32":
+                        for x in (synth.uniform_i32(n, seed), synth.mod_i32(n, seed, 7)):
+                            assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+                    elif kind == "f64":
+                        for dist in ("uniform", "few", "reverse"):
+                            x = synth.f64_config(dist, n, seed)
+                            assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+                    else:
+                        for dist in ("uniform", "mod1000"):
+                            k, v = synth.kv_config(dist, n, seed)
+                            gk, gv = _sort_dev(qs, k, v)
+                            ok, ov = oracle_sort(k, v)
+                            assert_kv_sorted_equal(k, v, gk, gv, ok, ov)
+    finally:
+        qs.set_option("leaf_max", 0)
+        qs.set_option("small_max", 0)
+        qs.set_option("ordered", 0)
