@@ -113,6 +113,24 @@ def test_sort_f64_infinities():
     assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
 
 
+@pytest.mark.parametrize("n", [3000, 50_000, 1 << 20])
+def test_sort_f64_extremes(n):
+    """FP64 keys at the ends of the bit-pattern order the integer compares rely
+    on: +-DBL_MAX, +-smallest normal, +-subnormals, +-1, mixed into uniform
+    keys; an all-equal array; an array of only two subnormals."""
+    qs = qs_gpu()
+    fi = np.finfo(np.float64)
+    special = np.array([fi.max, -fi.max, fi.tiny, -fi.tiny, 5e-324, -5e-324, 2.5e-310, -2.5e-310, 1.0, -1.0])
+    sel = synth.mod_i32(n, 21, 2 * special.size)
+    x = synth.uniform_f64(n, 22)
+    x = np.where(sel < special.size, special[np.minimum(sel, special.size - 1)], x)
+    assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
+    y = np.full(n, -3.75)
+    assert_keys_equal(_sort_dev(qs, y), oracle_sort(y))
+    z = np.where(synth.mod_i32(n, 23, 2) == 0, 5e-324, -5e-324)
+    assert_keys_equal(_sort_dev(qs, z), oracle_sort(z))
+
+
 @pytest.mark.parametrize("koff,voff", [(1, 1), (1, 2), (3, 0), (2, 2)])
 def test_sort_unaligned(koff, voff):
     qs = qs_gpu()
