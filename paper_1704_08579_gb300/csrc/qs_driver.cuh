@@ -523,8 +523,9 @@ __device__ __forceinline__ int count_low_any(const typename Tr::K *buf, uint64_t
 
 // ---------------------------------------------------------------------------
 // Release of a written tile (one thread, after a CTA barrier that follows the
-// tile's stores): its pivot-equal count, then an acq_rel add on the task's
-// tile counter (it releases the stores; the last adder acquires everyone's).
+// tile's stores): its pivot-equal count, then a gpu-scope fence and an add on
+// the task's tile counter (releasing the stores); the last adder fences again
+// to acquire everyone's.
 // The tile that arrives last completes the task, so no CTA ever waits for
 // the others.  The release is deferred into the next tile (see
 // partition_tile), where the stores have had time to drain.
