@@ -149,6 +149,29 @@ def _device_id(torch, local_rank):
         return vis.split(",")[local_rank] if vis else str(local_rank)
 
 
+def host_identity() -> dict:
+    """The host the CPU baseline runs on: logical CPUs and CPU model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model and os.path.exists("/proc/cpuinfo"):
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    import platform
+
+    return {"nproc": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
 def cpu_oracle_baseline(sample_log2: int = 24, repeats: int = 3, seed: int | None = None):
     """Times the oracle (single-threaded Appendix A quicksort) on the first
     2^sample_log2 keys of the workload's seeded stream."""
@@ -164,9 +187,9 @@ def cpu_oracle_baseline(sample_log2: int = 24, repeats: int = 3, seed: int | Non
         oracle.sort_inplace(y)
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
-    return {"value": n / t / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-            "sample": "first 2^%d keys of the same seeded f64 stream, oracle quicksort, median of %d runs "
-                      "(%.2f s each)" % (sample_log2, repeats, t)}
+    return dict({"value": n / t / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                 "sample": "first 2^%d keys of the same seeded f64 stream, oracle quicksort, median of %d runs "
+                           "(%.2f s each)" % (sample_log2, repeats, t)}, **host_identity())
 
 
 def run_reference(args):
@@ -195,8 +218,9 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_KEYS, "sample_n": n,
                    "note": "CPU oracle on a bounded sample of the workload (first 2^22 keys) per step"},
-        "cpu_baseline": {"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-                         "sample": "first 2^22 keys of the workload's seeded stream per step"},
+        "cpu_baseline": dict({"value": value, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                              "sample": "first 2^22 keys of the workload's seeded stream per step"},
+                             **host_identity()),
         "e2e": {"value": value, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -391,25 +415,38 @@ def _batched(torch, qs, stream, nseg=20_000, steps=3):
         ok = bool(((bk[0][1:] >= bk[0][:-1]) | (torch.isin(torch.arange(1, n, device="cuda"), doffs))).all())
         del bk, bv
         autotune.apply({})  # back to the compiled defaults for the plain form
-        # Plain form: one sort call (one launch sequence) per array.
+        # Plain form: one asynchronous sort call (one launch sequence) per
+        # array, no host synchronisation between them, one qs_sync_status at
+        # the end; the device time spans the whole sequence.
+        prof = qs.get_option("profile")
+        qs.set_option("profile", 0)  # profiling would make every call synchronous
         pk = dk.clone()
         pv = dv.clone() if dv is not None else None
         bounds = offs.tolist()
+        views = [(pk[bounds[i]:bounds[i + 1]], None if pv is None else pv[bounds[i]:bounds[i + 1]])
+                 for i in range(nseg) if bounds[i + 1] - bounds[i] > 1]
+        qs.reserve(n, kind)
         torch.cuda.synchronize()
         a2 = torch.cuda.Event(enable_timing=True)
         b2 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             a2.record(stream)
-            for i in range(nseg):
-                lo, hi = bounds[i], bounds[i + 1]
-                if hi - lo > 1:
-                    qs.sort(pk[lo:hi], None if pv is None else pv[lo:hi], stream=stream)
+            for k_view, v_view in views:
+                qs.sort(k_view, v_view, stream=stream, sync=False)
             b2.record(stream)
+        qs.sync_status(stream)
+        host_s = time.perf_counter() - t0
         b2.synchronize()
         ms_plain = a2.elapsed_time(b2)
+        qs.set_option("profile", prof)
+        plain_ok = bool(((pk[1:] >= pk[:-1]) | (torch.isin(torch.arange(1, n, device="cuda"), doffs))).all())
         out[kind] = {"workload": "%d %s arrays, sizes log-uniform [16, 2^18], %d keys" % (nseg, kind, n),
                      "batched_ms": ms_batched, "batched_gkeys_s": n / (ms_batched / 1e3) / 1e9,
                      "plain_per_array_ms": ms_plain, "plain_gkeys_s": n / (ms_plain / 1e3) / 1e9,
+                     "plain_form": "one asynchronous qs_sort_%s call per array, one qs_sync_status at the end"
+                                   % kind,
+                     "plain_host_issue_ms": host_s * 1e3, "plain_sorted": plain_ok,
                      "speedup": ms_plain / ms_batched, "tuned": {k: tuned[k] for k in ("leaf_max", "small_max", "driver_items")},
                      "batched_sorted": ok}
         del dk, dv, pk, pv
@@ -565,18 +602,23 @@ def run_partition_only(args):
     qs_build.build()
     x = synth.f64_config("uniform", N_KEYS)
     pivot = float(np.partition(x, N_KEYS // 2)[N_KEYS // 2])
-    d = torch.from_numpy(x).to("cuda")
-    bufs = [d.clone() for _ in range(args.warmup + args.steps + 1)]
-    del d
+    # One device copy of the input, restored from pinned host memory before
+    # every call (not timed): the device holds the input plus the library's
+    # scratch, nothing else.
+    pristine = torch.from_numpy(x).pin_memory()
+    d = torch.empty(N_KEYS, dtype=torch.float64, device="cuda")
+    qs.reserve(N_KEYS, "f64")
     qs.set_option("profile", 1)
     stream = torch.cuda.Stream()
     res = []
+    calls = args.warmup + args.steps + 1
     with torch.cuda.stream(stream):
-        for i, b in enumerate(bufs):
-            if i == len(bufs) - 1:
+        for i in range(calls):
+            d.copy_(pristine, non_blocking=True)
+            if i == calls - 1:
                 qs.set_option("profile", 2)  # cycle counters on the last, untimed call only
-            split = qs.partition(b, pivot, stream=stream)
-            if args.warmup <= i < len(bufs) - 1:
+            split = qs.partition(d, pivot, stream=stream)
+            if args.warmup <= i < calls - 1:
                 res.append(qs.stats())
         cycles = qs.stats()["driver_cycles"]
     qs.set_option("profile", 1)

@@ -18,17 +18,33 @@
  *   - n is an element count, 0 <= n <= 2^38.  n == 0 (and n == 1 for sorts)
  *     succeeds without touching memory.
  *   - stream is a cudaStream_t (NULL = the legacy default stream).  Work is
- *     issued on it, and every entry point returns only after that work has
- *     finished (it synchronises the stream once, to read the result/status).
+ *     issued on it.  qs_sort_* and qs_sort_segmented_* are ASYNCHRONOUS: they
+ *     return QS_OK once the work is enqueued (Algorithm 3's simd_QS is a plain
+ *     call with no result to wait for), and a device-side failure is reported
+ *     later, by qs_sync_status() or by the next call on the device.  Every
+ *     other entry point returns only after its work has finished (a partition
+ *     returns a split index, the host, learned and bucket forms read results
+ *     back).  QS_OPT_SYNC = 1, or profiling, makes the sorts synchronous too.
  *   - The library owns one workspace per device (scratch arrays of n keys and
  *     n values, a task queue, look-back words); it grows on demand or by
- *     qs_reserve(), and is guarded by a mutex, so concurrent calls on one
- *     device are serialised.
+ *     qs_reserve(), and is guarded by a mutex, so concurrent host calls on one
+ *     device are serialised.  Calls are also ordered on the GPU: each waits
+ *     (cudaStreamWaitEvent) for the previous call's last operation, whatever
+ *     stream that was issued on, so asynchronous calls on different streams
+ *     never overlap on the shared buffers.  A call that has to grow the
+ *     workspace (cudaMalloc/cudaFree) synchronises the device; qs_reserve()
+ *     beforehand avoids that.
  *   - f64 keys must contain no NaN and no -0.0 (not checked).
  *   - Errors: a negative qs_status; qs_last_error() then describes it.  A
  *     device-side failure (a bounded wait that ran out, a capacity overflow)
  *     leaves the array contents unspecified but a permutation is NOT
- *     guaranteed; the library stays usable.
+ *     guaranteed; the library stays usable.  A failure of an asynchronous
+ *     sort is kept in a device status word until it is reported once: by
+ *     qs_sync_status(), by a synchronous call, or by the next call that finds
+ *     the failed call finished (that call then returns the error and does no
+ *     work of its own); qs_last_error() says "an earlier asynchronous call
+ *     failed" when the error is not the returning call's own.  Only the first
+ *     failure between two reports is kept.
  */
 #ifndef QS_H_
 #define QS_H_
@@ -78,7 +94,10 @@ int64_t qs_partition_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, int32_t piv
  * each part into d_keys.  Keys equal to a pivot that can no longer be split
  * are finished as a block.  For kv the values follow their keys; the order of
  * values among equal keys is unspecified (the method is not stable).
- * Returns QS_OK or a negative qs_status.
+ * Asynchronous (see the conventions above): returns QS_OK once enqueued, or a
+ * negative qs_status for a bad argument, a failed launch or an earlier
+ * asynchronous call's failure.  d_keys (and d_vals) must stay valid until
+ * the work has finished.
  */
 int qs_sort_i32(int32_t *d_keys, int64_t n, qs_stream_t stream);
 int qs_sort_f64(double *d_keys, int64_t n, qs_stream_t stream);
@@ -92,7 +111,8 @@ int qs_sort_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, qs_stream_t stream);
  * QS_ERR_INVALID_ARG and leaves the keys unspecified).  All segments are sorted
  * by one setup pass, one launch of the persistent partition kernel and one
  * launch of the leaf kernel; these are captured once per argument set into a
- * CUDA graph and replayed.  Same method and return convention as qs_sort_*.
+ * CUDA graph and replayed.  Same method and return convention as qs_sort_*
+ * (asynchronous).
  */
 int qs_sort_segmented_i32(int32_t *d_keys, int64_t n, const int64_t *d_offsets, int64_t nseg,
                           qs_stream_t stream);
@@ -194,10 +214,11 @@ int qs_sort_host_kv(int32_t *h_keys, int32_t *h_vals, int64_t n, qs_stream_t str
  * cannot let them.  This variant allocates nothing: its scratch is one fixed
  * file-scope device array of about 4.2 MiB that every GPU loading the library
  * holds until the process exits.
- *   - Same operation, arguments, result order and return value as
- *     qs_partition_i32, for 0 <= n <= QS_NOALLOC_MAX_N; a larger n returns
- *     QS_ERR_INVALID_ARG.  Errors come back as a negative qs_status only
- *     (qs_last_error is not updated).
+ *   - Same operation, arguments, result order, return value and wait limit
+ *     (QS_OPT_WAIT_LIMIT_NS) as qs_partition_i32, for 0 <= n <=
+ *     QS_NOALLOC_MAX_N; a larger n returns QS_ERR_INVALID_ARG.  Errors come
+ *     back as a negative qs_status only (qs_last_error is not updated).
+ *     Synchronous, like qs_partition_i32.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) and the grid size; make that first call before
  *     any stream capture.
@@ -218,6 +239,15 @@ int qs_reserve(int64_t n, int kind);
 /* Frees the current device's workspace (a later call re-creates it). */
 void qs_release(void);
 
+/*
+ * Waits until every call issued on this device's workspace, and all work on
+ * `stream`, has finished; then returns QS_OK, or the first device-side failure
+ * of an asynchronous call that has not been reported yet (which is then
+ * cleared).  Afterwards qs_get_stats() holds the device counters of the last
+ * call.  This is the synchronisation point of the asynchronous sorts.
+ */
+int qs_sync_status(qs_stream_t stream);
+
 /* Text of the last error raised on this host thread ("" if none). */
 const char *qs_last_error(void);
 
@@ -225,7 +255,8 @@ const char *qs_last_error(void);
 int qs_version(void);
 
 /*
- * Counters of the last qs_sort_* / qs_partition_* call on this host thread.
+ * Counters of the last qs_sort_* / qs_partition_* call on this host thread
+ * (for an asynchronous sort: once qs_sync_status() has returned).
  * The byte figures let a caller compute the HBM traffic the schedule moves:
  * every element of a device-wide partition is read once and written once,
  * so are leaf-sorted and copied elements.
@@ -309,6 +340,9 @@ int qs_get_stats(qs_stats *out);
  *                        qs_partition_* (which always does so).  The sorted
  *                        keys are the same either way; with key/value pairs
  *                        the order of the values of equal keys may differ.
+ *   QS_OPT_SYNC          1: qs_sort_* and qs_sort_segmented_* return only
+ *                        after their work has finished, with its status;
+ *                        0 (default): they are asynchronous.
  * The tuning options are what the autotuner (paper_1704_08579_gb300.autotune)
  * searches.
  */
@@ -320,9 +354,13 @@ enum {
     QS_OPT_LEAF_MAX = 5,
     QS_OPT_SMALL_MAX = 6,
     QS_OPT_DRIVER_ITEMS = 7,
-    QS_OPT_ORDERED = 8
+    QS_OPT_ORDERED = 8,
+    QS_OPT_SYNC = 9
 };
 int qs_set_option(int option, int64_t value);
+/* Current value of an option (as set, 0 = the default) into *value; returns
+ * QS_OK, or QS_ERR_INVALID_ARG for an unknown option or a NULL pointer. */
+int qs_get_option(int option, int64_t *value);
 
 #ifdef __cplusplus
 }

@@ -4,8 +4,14 @@ Argument marshalling only: every step of partitioning and sorting runs in the
 library's CUDA kernels.  The names follow the C-ABI in ``include/qs.h``:
 
     partition(keys, pivot, values=None)  -> split index   (qs_partition_*)
-    sort(keys, values=None)                               (qs_sort_*)
+    sort(keys, values=None, sync=True)                    (qs_sort_*)
     sort_host(keys, values=None)                          (qs_sort_host_*)
+    sync_status(stream=None)                              (qs_sync_status)
+
+The C sorts are asynchronous; ``sort``/``sort_segmented`` call
+``qs_sync_status`` after them (raising on a device-side failure) unless
+``sync=False`` is passed, in which case a failure is raised by a later
+``sync_status`` or by the next call.
 
 ``keys``/``values`` are contiguous CUDA tensors (int32 or float64 keys, int32
 values) for ``partition``/``sort`` and contiguous numpy arrays for
@@ -31,7 +37,7 @@ STATUS = {
 }
 KIND = {"i32": 0, "f64": 1, "kv": 2}
 OPTION = {"profile": 1, "wait_limit_ns": 2, "task_cap": 3, "driver_ctas": 4, "leaf_max": 5, "small_max": 6,
-          "driver_items": 7, "ordered": 8}
+          "driver_items": 7, "ordered": 8, "sync": 9}
 
 _lib = None
 _lock = threading.Lock()
@@ -94,12 +100,14 @@ def load() -> ctypes.CDLL:
             "qs_sort_host_i32": ([vp, i64, vp], ci),
             "qs_sort_host_f64": ([vp, i64, vp], ci),
             "qs_sort_host_kv": ([vp, vp, i64, vp], ci),
+            "qs_sync_status": ([vp], ci),
             "qs_reserve": ([i64, ci], ci),
             "qs_release": ([], None),
             "qs_last_error": ([], ctypes.c_char_p),
             "qs_version": ([], ci),
             "qs_get_stats": ([ctypes.POINTER(Stats)], ci),
             "qs_set_option": ([ci, i64], ci),
+            "qs_get_option": ([ci, ctypes.POINTER(i64)], ci),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -165,8 +173,15 @@ def partition(keys, pivot, values=None, stream=None) -> int:
     return _check(lib.qs_partition_f64(keys.data_ptr(), n, float(pivot), s))
 
 
-def sort(keys, values=None, stream=None) -> None:
-    """qs_sort_*: sorts keys (and values with them) in place."""
+def sync_status(stream=None) -> None:
+    """qs_sync_status: waits for the library's work and for `stream`; raises
+    the first device-side failure of an asynchronous call not reported yet."""
+    _check(load().qs_sync_status(_stream_handle(stream)))
+
+
+def sort(keys, values=None, stream=None, sync=True) -> None:
+    """qs_sort_*: sorts keys (and values with them) in place; with
+    sync=False it returns once the work is enqueued."""
     lib = load()
     kind = _kind_of(keys, values)
     _check_tensor(keys, "keys")
@@ -181,9 +196,11 @@ def sort(keys, values=None, stream=None) -> None:
         _check(lib.qs_sort_i32(keys.data_ptr(), n, s))
     else:
         _check(lib.qs_sort_f64(keys.data_ptr(), n, s))
+    if sync:
+        _check(lib.qs_sync_status(s))
 
 
-def sort_segmented(keys, offsets, values=None, stream=None) -> None:
+def sort_segmented(keys, offsets, values=None, stream=None, sync=True) -> None:
     """qs_sort_segmented_*: sorts every segment [offsets[i], offsets[i+1]) of keys in place.
 
     ``offsets`` is a CUDA int64 tensor of nseg + 1 entries."""
@@ -207,6 +224,8 @@ def sort_segmented(keys, offsets, values=None, stream=None) -> None:
         _check(lib.qs_sort_segmented_i32(keys.data_ptr(), n, offsets.data_ptr(), nseg, s))
     else:
         _check(lib.qs_sort_segmented_f64(keys.data_ptr(), n, offsets.data_ptr(), nseg, s))
+    if sync:
+        _check(lib.qs_sync_status(s))
 
 
 def _ptr(t):
@@ -325,6 +344,12 @@ def release() -> None:
 
 def set_option(name: str, value: int) -> None:
     _check(load().qs_set_option(OPTION[name], int(value)))
+
+
+def get_option(name: str) -> int:
+    v = ctypes.c_int64(0)
+    _check(load().qs_get_option(OPTION[name], ctypes.byref(v)))
+    return v.value
 
 
 def stats() -> dict:

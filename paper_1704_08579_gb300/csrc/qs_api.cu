@@ -5,6 +5,7 @@
 
 #include <atomic>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -29,6 +30,7 @@ std::atomic<int64_t> g_leaf_max{0};   // 0 = the kind's compiled maximum
 std::atomic<int64_t> g_small_max{0};  // 0 = the kind's compiled maximum
 std::atomic<int64_t> g_driver_items{0};  // 0 = the kind's default partition tile
 std::atomic<int> g_ordered{0};  // 1 = the sort's partitions place tiles in input order too
+std::atomic<int> g_sync{0};     // 1 = sorts return only after their work has finished
 
 constexpr int64_t kMaxN = 1ll << 38;
 
@@ -69,6 +71,13 @@ struct Workspace {
     Ctrl *h_ctrl = nullptr;
     bool dirty = true;  // look-back words / ticket owners must be cleared before use
     cudaEvent_t ev[6] = {};
+    // Ordering of calls on this workspace: every call waits (on its own
+    // stream) for `done`, recorded after the previous call's last operation,
+    // so calls on different streams never overlap on the shared buffers.
+    cudaEvent_t done = nullptr;
+    bool done_recorded = false;
+    bool unreported = false;  // the last call's status (copied to h_ctrl) has not been examined
+    int64_t last_grid_driver = 0, last_grid_leaf = 0, last_n = 0, last_kind = 0;
     cudaStream_t capture = nullptr;  // private stream used to capture CUDA graphs
     void *aux = nullptr;                   // learned-splitter / bucket state
     LearnedState *h_learned = nullptr;     // pinned copy of its state
@@ -151,6 +160,10 @@ int ws_init(Workspace &w)
         e = cudaEventCreate(&ev);
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     }
+    e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    w.done_recorded = false;
+    w.unreported = false;
     w.init = true;
     return QS_OK;
 }
@@ -246,6 +259,10 @@ void ws_free(Workspace &w)
     if (w.h_ctrl) cudaFreeHost(w.h_ctrl);
     for (auto &ev : w.ev)
         if (ev) cudaEventDestroy(ev);
+    if (w.done) cudaEventDestroy(w.done);
+    w.done = nullptr;
+    w.done_recorded = false;
+    w.unreported = false;
     w.scratch_k = w.scratch_v = w.stage_k = w.stage_v = nullptr;
     w.scratch_k_bytes = w.scratch_v_bytes = w.stage_k_bytes = w.stage_v_bytes = 0;
     w.tasks = nullptr;
@@ -307,11 +324,87 @@ Args<K, int32_t> make_args(Workspace &w, int kind, K *keys, int32_t *vals, int64
     return a;
 }
 
+// Ordering of the calls that share a workspace: `s` waits for the last
+// operation of the previous call, whatever stream it was issued on.
+cudaError_t order_after_previous(Workspace &w, cudaStream_t s)
+{
+    return w.done_recorded ? cudaStreamWaitEvent(s, w.done, 0) : cudaSuccess;
+}
+
+cudaError_t mark_done(Workspace &w, cudaStream_t s)
+{
+    const cudaError_t e = cudaEventRecord(w.done, s);
+    if (e == cudaSuccess) w.done_recorded = true;
+    return e;
+}
+
+// Device counters of the last finished call (read from the control block it
+// copied back) into this thread's statistics.
+void stats_from_ctrl(const Workspace &w)
+{
+    const Ctrl &c = *w.h_ctrl;
+    t_stats.n = w.last_n;
+    t_stats.kind = w.last_kind;
+    t_stats.part_tasks = static_cast<int64_t>(c.part_tasks);
+    t_stats.part_keys = static_cast<int64_t>(c.part_keys);
+    t_stats.leaf_parts = static_cast<int64_t>(c.leaf_parts);
+    t_stats.leaf_keys = static_cast<int64_t>(c.leaf_keys);
+    t_stats.copy_keys = static_cast<int64_t>(c.copy_keys);
+    t_stats.max_depth = static_cast<int64_t>(c.max_depth);
+    t_stats.lookback_words = static_cast<int64_t>(c.pool_cursor);
+    t_stats.grid_driver = w.last_grid_driver;
+    t_stats.grid_leaf = w.last_grid_leaf;
+    for (int i = 0; i < kProfSlots; ++i) t_stats.driver_cycles[i] = static_cast<int64_t>(c.cycles[i]);
+}
+
+// Examines the status that the last call copied back (its work has
+// finished).  Returns QS_OK, or the first device-side error not reported yet
+// -- an earlier asynchronous call's (kept in the sticky word by the setup
+// kernel of the calls after it) or the last call's -- and clears it on the
+// device, so each failure is reported once.
+int report_status(Workspace &w, cudaStream_t s)
+{
+    static_assert(offsetof(Ctrl, sticky_info) == offsetof(Ctrl, status) + 3 * sizeof(int),
+                  "status, info, sticky, sticky_info are contiguous");
+    w.unreported = false;
+    Ctrl &c = *w.h_ctrl;
+    const bool earlier = c.sticky != 0;
+    const int err = earlier ? c.sticky : c.status;
+    if (err == 0) return QS_OK;
+    const int info = earlier ? c.sticky_info : c.info;
+    c.status = c.sticky = 0;
+    w.dirty = true;  // look-back words and ticket owners are cleared before the next call
+    cudaError_t e = cudaMemsetAsync(&w.ctrl->status, 0, 4 * sizeof(int), s);
+    if (e == cudaSuccess) e = mark_done(w, s);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the status word");
+    return fail(err, "%s%s (code %d, detail %d)", earlier ? "an earlier asynchronous call failed: " : "",
+                status_text(err), err, info);
+}
+
+// Before a call enqueues work: an earlier asynchronous call that has finished
+// with an error is reported now, and the new call does nothing.
+int check_earlier(Workspace &w, cudaStream_t s)
+{
+    if (!w.unreported || !w.done_recorded) return QS_OK;
+    const cudaError_t q = cudaEventQuery(w.done);
+    if (q == cudaErrorNotReady) {
+        if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+        return QS_OK;  // still running: its error, if any, is kept on the device
+    }
+    if (q != cudaSuccess) return cuda_fail(q, "cudaEventQuery");
+    stats_from_ctrl(w);
+    return report_status(w, s);
+}
+
 // Runs one sort (partition_only = 0) or partition (1) of kind `kind` on the
-// current device.  keys/vals are device pointers.
+// current device.  keys/vals are device pointers.  A partition, a call with
+// profiling on, a call with QS_OPT_SYNC = 1 and a call with force_sync
+// return after the work has finished; other sorts return once it is
+// enqueued (asynchronous: the status is read by qs_sync_status or reported
+// by the next call).
 template <class K>
 int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, int partition_only,
-            qs_stream_t stream, const int64_t *seg_off = nullptr, int64_t nseg = 0)
+            qs_stream_t stream, const int64_t *seg_off = nullptr, int64_t nseg = 0, bool force_sync = false)
 {
     t_error.clear();
     std::memset(&t_stats, 0, sizeof(t_stats));
@@ -339,6 +432,8 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     int rc = ws_ensure(w, n, kind, nseg);
     if (rc) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((rc = check_earlier(w, s))) return rc;
+    if ((e = order_after_previous(w, s)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
     if (w.dirty) {
         if ((e = cudaMemsetAsync(w.pool, 0, static_cast<size_t>(w.pool_cap) * 8, s)) != cudaSuccess)
             return cuda_fail(e, "cudaMemsetAsync");
@@ -346,36 +441,12 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
             return cuda_fail(e, "cudaMemsetAsync");
         w.dirty = false;
     }
-    const KernelLimits lim = limits_of(kind);
-    Args<K, int32_t> a;
-    std::memset(&a, 0, sizeof(a));
-    a.keys[0] = keys;
-    a.keys[1] = static_cast<K *>(w.scratch_k);
-    a.vals[0] = vals;
-    a.vals[1] = kind == QS_KIND_KV ? static_cast<int32_t *>(w.scratch_v) : nullptr;
-    for (int b = 0; b < 2; ++b) {
-        a.key_phase[b] = phase_of<K>(a.keys[b]);
-        a.val_vec[b] = a.vals[b] ? (phase_of<int32_t>(a.vals[b]) == a.key_phase[b]) : 1;
-    }
-    a.n = n;
-    a.tasks = w.tasks;
-    a.owner = w.owner;
-    a.pool = w.pool;
-    a.leaves = w.leaves;
-    a.ctrl = w.ctrl;
-    a.task_cap = w.task_cap;
-    a.pool_cap = w.pool_cap;
-    a.leaf_cap = w.leaf_cap;
-    a.leaf_max = leaf_max_of(kind);
-    a.small_max = small_max_of(kind);
-    a.wait_limit_ns = static_cast<uint64_t>(g_wait_limit_ns.load());
+    Args<K, int32_t> a = make_args<K>(w, kind, keys, vals, n);
     a.pivot_bits = pivot_bits;
     a.partition_only = partition_only;
-    a.ordered = partition_only ? 1 : g_ordered.load();
-    a.profile = g_profile.load() >= 2 ? 1 : 0;
+    if (partition_only) a.ordered = 1;
     a.seg_off = seg_off;
     a.nseg = nseg;
-    (void)lim;
 
     LaunchCfg cfg;
     std::memset(&cfg, 0, sizeof(cfg));
@@ -435,22 +506,20 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     } else {
         if ((e = enqueue(s)) != cudaSuccess) return cuda_fail(e, "kernel launch");
     }
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    const Ctrl &c = *w.h_ctrl;
-    t_stats.part_tasks = static_cast<int64_t>(c.part_tasks);
-    t_stats.part_keys = static_cast<int64_t>(c.part_keys);
-    t_stats.leaf_parts = static_cast<int64_t>(c.leaf_parts);
-    t_stats.leaf_keys = static_cast<int64_t>(c.leaf_keys);
-    t_stats.copy_keys = static_cast<int64_t>(c.copy_keys);
-    t_stats.max_depth = static_cast<int64_t>(c.max_depth);
-    t_stats.lookback_words = static_cast<int64_t>(c.pool_cursor);
+    if ((e = mark_done(w, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    w.unreported = true;
+    w.last_n = n;
+    w.last_kind = kind;
+    w.last_grid_driver = cfg.grid_driver;
+    w.last_grid_leaf = cfg.grid_leaf;
     t_stats.grid_driver = cfg.grid_driver;
     t_stats.grid_leaf = cfg.grid_leaf;
-    for (int i = 0; i < kProfSlots; ++i) t_stats.driver_cycles[i] = static_cast<int64_t>(c.cycles[i]);
-    if (c.status != 0) {
-        w.dirty = true;
-        return fail(c.status, "%s (code %d, detail %d)", status_text(c.status), c.status, c.info);
-    }
+    if (!(partition_only || force_sync || cfg.profile || g_sync.load())) return QS_OK;
+
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    stats_from_ctrl(w);
+    const unsigned long long lt = w.h_ctrl->lt_result;
+    if ((rc = report_status(w, s))) return rc;
     if (partition_only) {
         // The split is known; move the partitioned data back into the caller's arrays.
         if (cfg.profile) cudaEventRecord(w.ev[4], s);
@@ -460,6 +529,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
             (e = cudaMemcpyAsync(vals, w.scratch_v, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return cuda_fail(e, "cudaMemcpyAsync(copy-back)");
         if (cfg.profile) cudaEventRecord(w.ev[5], s);
+        if ((e = mark_done(w, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     }
     if (cfg.profile) {
@@ -469,7 +539,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
         if (partition_only && cudaEventElapsedTime(&ms, w.ev[4], w.ev[5]) == cudaSuccess) t_stats.ms_copy = ms;
         if (cudaEventElapsedTime(&ms, w.ev[0], partition_only ? w.ev[5] : w.ev[3]) == cudaSuccess) t_stats.ms_total = ms;
     }
-    return partition_only ? static_cast<int64_t>(c.lt_result) : QS_OK;
+    return partition_only ? static_cast<int64_t>(lt) : QS_OK;
 }
 
 template <class K>
@@ -502,7 +572,7 @@ int run_host(int kind, K *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream
     if (kind == QS_KIND_KV &&
         (e = cudaMemcpyAsync(dv, h_vals, static_cast<size_t>(n) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync(H2D)");
-    const int64_t rc = run<K>(kind, dk, kind == QS_KIND_KV ? dv : nullptr, n, 0, 0, stream);
+    const int64_t rc = run<K>(kind, dk, kind == QS_KIND_KV ? dv : nullptr, n, 0, 0, stream, nullptr, 0, true);
     if (rc) return static_cast<int>(rc);
     if ((e = cudaMemcpyAsync(h_keys, dk, static_cast<size_t>(n) * sizeof(K), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync(D2H)");
@@ -571,7 +641,7 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     }
     if (op == kOpSortLearned && n < (1 << 16)) {
         // Too small for 256 buckets to pay: the plain method.
-        return static_cast<int>(run<K>(kind, keys, nullptr, n, 0, 0, stream));
+        return static_cast<int>(run<K>(kind, keys, nullptr, n, 0, 0, stream, nullptr, 0, true));
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -583,6 +653,8 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     if (rc) return rc;
     if ((rc = aux_ensure(w))) return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if ((rc = check_earlier(w, s))) return rc;
+    if ((e = order_after_previous(w, s)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
     if (w.dirty) {
         if ((e = cudaMemsetAsync(w.pool, 0, static_cast<size_t>(w.pool_cap) * 8, s)) != cudaSuccess ||
             (e = cudaMemsetAsync(w.owner, 0, static_cast<size_t>(w.pool_cap) * 4, s)) != cudaSuccess)
@@ -622,23 +694,18 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     if ((e = cudaMemcpyAsync(w.h_learned, lc.p.st, sizeof(LearnedState), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(w.h_ctrl, w.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync(status)");
+    if ((e = mark_done(w, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+    w.unreported = true;
+    w.last_n = n;
+    w.last_kind = kind;
+    w.last_grid_driver = cfg.grid_driver;
+    w.last_grid_leaf = cfg.grid_leaf;
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (op == kOpSortLearned) stats_from_ctrl(w);
+    if ((rc = report_status(w, s))) return rc;
     const LearnedState &ls = *w.h_learned;
     if (ls.status != 0) return fail(QS_ERR_INTERNAL, "bucket pass index check failed");
     if (op == kOpSortLearned) {
-        const Ctrl &c = *w.h_ctrl;
-        t_stats.part_tasks = static_cast<int64_t>(c.part_tasks);
-        t_stats.part_keys = static_cast<int64_t>(c.part_keys);
-        t_stats.leaf_parts = static_cast<int64_t>(c.leaf_parts);
-        t_stats.leaf_keys = static_cast<int64_t>(c.leaf_keys);
-        t_stats.copy_keys = static_cast<int64_t>(c.copy_keys);
-        t_stats.max_depth = static_cast<int64_t>(c.max_depth);
-        t_stats.grid_driver = cfg.grid_driver;
-        t_stats.grid_leaf = cfg.grid_leaf;
-        if (c.status != 0) {
-            w.dirty = true;
-            return fail(c.status, "%s (code %d, detail %d)", status_text(c.status), c.status, c.info);
-        }
         if (cfg.profile) {
             float ms = 0;
             if (cudaEventElapsedTime(&ms, w.ev[1], w.ev[2]) == cudaSuccess) t_stats.ms_driver = ms;
@@ -655,7 +722,7 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
                 cudaSuccess ||
             (e = cudaMemcpyAsync(bucket_off_out, lc.p.st->bucket_off, sizeof(int64_t) * (nsplit + 2),
                                  cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
-            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            (e = mark_done(w, s)) != cudaSuccess || (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return cuda_fail(e, "copy-back");
     }
     return QS_OK;
@@ -671,6 +738,9 @@ uint64_t bits_f64(double k)
 }
 
 }  // namespace
+
+uint64_t option_wait_limit_ns() { return static_cast<uint64_t>(g_wait_limit_ns.load()); }
+
 }  // namespace qs
 
 using namespace qs;
@@ -830,6 +900,26 @@ void qs_release(void)
     ws_free(w);
 }
 
+int qs_sync_status(qs_stream_t stream)
+{
+    t_error.clear();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(QS_ERR_INVALID_ARG, "device %d out of range", dev);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Workspace &w = *workspace_for(dev);
+    std::lock_guard<std::mutex> guard(w.mu);
+    if (w.init && w.done_recorded && (e = cudaEventSynchronize(w.done)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventSynchronize");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (!w.init || !w.unreported) return QS_OK;
+    stats_from_ctrl(w);
+    const int rc = report_status(w, s);
+    if (rc && (e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return rc;
+}
+
 const char *qs_last_error(void) { return t_error.c_str(); }
 
 int qs_version(void) { return 100; }
@@ -868,6 +958,10 @@ int qs_set_option(int option, int64_t value)
         if (value < 0 || value > 1) return QS_ERR_INVALID_ARG;
         g_ordered = static_cast<int>(value);
         return QS_OK;
+    case QS_OPT_SYNC:
+        if (value < 0 || value > 1) return QS_ERR_INVALID_ARG;
+        g_sync = static_cast<int>(value);
+        return QS_OK;
     case QS_OPT_LEAF_MAX:
     case QS_OPT_SMALL_MAX:
         if (value < 0 || (value > 0 && (value < 32 || (value & (value - 1))))) return QS_ERR_INVALID_ARG;
@@ -875,6 +969,23 @@ int qs_set_option(int option, int64_t value)
         return QS_OK;
     default:
         return QS_ERR_INVALID_ARG;
+    }
+}
+
+int qs_get_option(int option, int64_t *value)
+{
+    if (!value) return QS_ERR_INVALID_ARG;
+    switch (option) {
+    case QS_OPT_PROFILE: *value = g_profile.load(); return QS_OK;
+    case QS_OPT_WAIT_LIMIT_NS: *value = g_wait_limit_ns.load(); return QS_OK;
+    case QS_OPT_TASK_CAP: *value = g_task_cap.load(); return QS_OK;
+    case QS_OPT_DRIVER_CTAS: *value = g_driver_ctas.load(); return QS_OK;
+    case QS_OPT_LEAF_MAX: *value = g_leaf_max.load(); return QS_OK;
+    case QS_OPT_SMALL_MAX: *value = g_small_max.load(); return QS_OK;
+    case QS_OPT_DRIVER_ITEMS: *value = g_driver_items.load(); return QS_OK;
+    case QS_OPT_ORDERED: *value = g_ordered.load(); return QS_OK;
+    case QS_OPT_SYNC: *value = g_sync.load(); return QS_OK;
+    default: return QS_ERR_INVALID_ARG;
     }
 }
 

@@ -244,8 +244,13 @@ __device__ __forceinline__ void set_error(Ctrl *c, int code, int info)
     if (atomicCAS(&c->status, 0, code) == 0) c->info = info;
 }
 
-// Bounded wait on an mbarrier phase by every thread of the CTA.  Returns
-// false if the limit ran out (the error is recorded).
+// Least time a CTA waits, before it exits, for a bulk copy it issued into
+// its own shared memory (whatever QS_OPT_WAIT_LIMIT_NS says).
+constexpr uint64_t kDrainFloorNs = 500000000ull;
+
+// Bounded wait on an mbarrier phase by one thread.  Returns false if the
+// limit ran out (the error is recorded); the decision is this thread's own,
+// so callers inside a barrier sequence make it CTA-uniform before acting.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity, Ctrl *c, uint64_t limit_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;

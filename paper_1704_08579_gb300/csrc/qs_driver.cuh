@@ -566,7 +566,9 @@ __device__ __forceinline__ void release_prev(const Args<typename Tr::K, typename
 // scan of the (k, warp) counts plus the look-back (ordered placement) or the
 // tile's two range claims (unordered) give its global position.
 // Keys are staged in shared memory in output order and written with
-// coalesced stores.  Returns 0, or -1 on abort.  On return sm.prev_last says
+// coalesced stores.  Returns 0; -1 when the wait for the tile's bulk copy
+// ran out (that copy may still be in flight); -2 on any other abort.  On
+// return sm.prev_last says
 // whether the deferred release of the previous tile completed its task
 // (sm.wf), which the caller then completes.
 // ---------------------------------------------------------------------------
@@ -611,26 +613,39 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     K key[E];
     V val[Tr::KV ? E : 1];
     uint32_t validm = 0;
+    // A timed-out wait is a per-thread event.  The thread that saw it keeps
+    // going with no keys (every warp still takes part in every ballot and
+    // barrier below), and the whole CTA abandons the tile at the barrier
+    // after the ballots (__syncthreads_or), so no thread leaves a barrier
+    // sequence the others are in.  The phase bit is flipped only once the
+    // whole CTA has consumed the phase; on abort it stays, so the exit drain
+    // waits for the very copy that was late.
+    bool landed = true;
     if (w.full) {
-        if (!mbar_wait_bounded(&sm.bar[b], (phases >> b) & 1u, a.ctrl, a.wait_limit_ns)) return -1;
-        phases ^= 1u << b;
+        landed = mbar_wait_bounded(&sm.bar[b], (phases >> b) & 1u, a.ctrl, a.wait_limit_ns);
         QS_TICK(1);
         const Vec *sv = reinterpret_cast<const Vec *>(sm.kbuf[b]);
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
             K tmp[VW];
-            Ops::split(sv[k * kDThreads + tid], tmp);
+            if (landed) {
+                Ops::split(sv[k * kDThreads + tid], tmp);
+            } else {
+#pragma unroll
+                for (int j = 0; j < VW; ++j) tmp[j] = K(0);
+            }
 #pragma unroll
             for (int j = 0; j < VW; ++j) key[k * VW + j] = tmp[j];
             if constexpr (Tr::KV) {
-                const int4 vv = reinterpret_cast<const int4 *>(sm.vbuf[b])[k * kDThreads + tid];
+                const int4 vv = landed ? reinterpret_cast<const int4 *>(sm.vbuf[b])[k * kDThreads + tid]
+                                       : make_int4(0, 0, 0, 0);
                 val[k * VW + 0] = vv.x;
                 val[k * VW + 1] = vv.y;
                 val[k * VW + 2] = vv.z;
                 val[k * VW + 3] = vv.w;
             }
         }
-        validm = E == 32 ? 0xffffffffu : ((1u << E) - 1u);
+        validm = landed ? (E == 32 ? 0xffffffffu : ((1u << E) - 1u)) : 0u;
     } else {
         const K *__restrict__ sk = a.keys[w.src];
         const V *__restrict__ svv = a.vals[w.src];
@@ -668,7 +683,8 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     for (int o = 16; o > 0; o >>= 1) eq += __shfl_xor_sync(0xffffffffu, eq, o);
     if (lane == 0 && eq) atomicAdd(&sm.eq_total, eq);
     if (a.profile && tid == 0) sm.tm[18] += prof_clock() - tprev;  // own work, before the barrier
-    __syncthreads();
+    if (__syncthreads_or(landed ? 0 : 1)) return -1;  // CTA-uniform: some thread's wait ran out
+    if (w.full) phases ^= 1u << b;
     QS_TICK(2);
     const long long tph = a.profile ? prof_clock() : 0;  // start of the placement phase
 
@@ -820,7 +836,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     }
     __syncthreads();
     QS_TICK(3);
-    if (sm.abort) return -1;
+    if (sm.abort) return -2;  // the tile's keys were consumed; the look-back gave up
     const int L = sm.low_total;
     const long long excl = sm.excl;
 
@@ -1066,7 +1082,7 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
             }
         }
         const int r = partition_tile<Tr>(a, sm.w[0], sm.w[1], sm, b, phases);
-        pending &= ~(1u << b);
+        if (r != -1) pending &= ~(1u << b);  // -1: the copy into buffer b was never seen to land
         if (sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);  // written before the tile's barriers
         if (r < 0) {
             aborted = true;
@@ -1097,9 +1113,16 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
         b ^= 1;
     }
     if (!aborted) flush_release<Tr>(a, sm);
-    // Never leave while a bulk copy may still be writing this CTA's shared memory.
+    // Never leave while a bulk copy may still be writing this CTA's shared
+    // memory: the next CTA on this SM could receive it.  `pending` and
+    // `phases` are the same in every thread (both change only at points the
+    // whole CTA passes together), so every thread waits for the same copies.
+    // A copy that was issued always lands, within microseconds; the wait's
+    // floor of kDrainFloorNs keeps a small QS_OPT_WAIT_LIMIT_NS from cutting
+    // it short (a timed-out drain records QS_ERR_TIMEOUT like any wait).
+    const uint64_t drain_ns = a.wait_limit_ns > kDrainFloorNs ? a.wait_limit_ns : kDrainFloorNs;
     for (int i = 0; i < 2; ++i)
-        if ((pending >> i) & 1u) mbar_wait_bounded(&sm.bar[i], (phases >> i) & 1u, a.ctrl, a.wait_limit_ns);
+        if ((pending >> i) & 1u) mbar_wait_bounded(&sm.bar[i], (phases >> i) & 1u, a.ctrl, drain_ns);
     __syncthreads();
     if (a.profile && tid == 0)
         for (int i = 0; i < kProfSlots; ++i) atomicAdd(&a.ctrl->cycles[i], static_cast<unsigned long long>(sm.tm[i]));
@@ -1134,6 +1157,12 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(Args<typename Tr::K, ty
         c->pending = 0;
         c->n_large = c->n_small = 0;
         c->claim_large = c->claim_small = 0;
+        // An error of the previous call that the host has not read yet is
+        // kept (asynchronous calls report it at the next synchronisation).
+        if (c->status != 0 && c->sticky == 0) {
+            c->sticky = c->status;
+            c->sticky_info = c->info;
+        }
         c->status = 0;
         c->info = 0;
         c->part_tasks = c->part_keys = c->leaf_parts = c->leaf_keys = c->copy_keys = c->max_depth = 0;

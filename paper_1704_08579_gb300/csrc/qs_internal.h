@@ -75,6 +75,7 @@ struct alignas(128) Ctrl {
     unsigned long long n_large, n_small;
     unsigned long long claim_large, claim_small;
     int status, info;
+    int sticky, sticky_info;  // first error of an earlier call not yet reported to the host
     // statistics
     unsigned long long part_tasks, part_keys, leaf_parts, leaf_keys, copy_keys, max_depth;
     unsigned long long lt_result;  // split index of a partition-only call
@@ -176,6 +177,8 @@ int mlp_forward(const float *P, const float *X, int64_t batch, float *Q, float *
 int mlp_backward(const float *P, const float *X, const float *T, const float *ACT, int64_t batch, float *WORK,
                  float *G, float *loss, void *stream);
 int mlp_adam(float *P, const float *G, float *M, float *V, int64_t step, float lr, void *stream);
+// Current QS_OPT_WAIT_LIMIT_NS (shared by every entry point).
+uint64_t option_wait_limit_ns();
 KernelLimits limits_i32();
 KernelLimits limits_f64();
 KernelLimits limits_kv();

@@ -183,7 +183,20 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) sm.idx = ld_relaxed_s32(&c->status);
     __syncthreads();
-    if (sm.idx != 0) return;  // the partition phase failed; leave the data alone
+    if (sm.idx != 0) {
+        // The partition phase failed: leave the data alone, but clear the
+        // look-back words and ticket owners it used (a failed persistent
+        // kernel leaves them set), so that the next call -- possibly issued
+        // before the host has seen this error -- starts from a clean state.
+        unsigned long long used = ld_relaxed_u64(&c->pool_cursor);
+        if (used > static_cast<unsigned long long>(a.pool_cap)) used = static_cast<unsigned long long>(a.pool_cap);
+        const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * kThreads;
+        for (unsigned long long i = static_cast<unsigned long long>(blockIdx.x) * kThreads + tid; i < used; i += stride) {
+            a.pool[i] = 0;
+            a.owner[i] = 0;
+        }
+        return;
+    }
     __syncthreads();
     const long long n_large = static_cast<long long>(ld_relaxed_u64(&c->n_large));
     const long long n_small = static_cast<long long>(ld_relaxed_u64(&c->n_small));

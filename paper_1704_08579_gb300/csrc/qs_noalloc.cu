@@ -68,8 +68,8 @@ extern "C" int64_t qs_partition_i32_noalloc(int32_t *d_keys, int64_t n, int32_t 
     if (!d_keys) return fail(QS_ERR_INVALID_ARG, "null key pointer");
     if (reinterpret_cast<uintptr_t>(d_keys) % 4) return fail(QS_ERR_ALIGN, "keys not aligned to 4 bytes");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return fail(QS_ERR_CUDA, "cudaGetDevice failed");
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(QS_ERR_CUDA, "cudaGetDevice failed");
+    if (dev < 0 || dev >= kMaxDevices) return fail(QS_ERR_INVALID_ARG, "device index out of range");
     std::lock_guard<std::mutex> guard(g_mu);  // calls share the one scratch array
     DeviceSetup &su = g_setup[dev];
     if (!su.ready) {
@@ -87,8 +87,9 @@ extern "C" int64_t qs_partition_i32_noalloc(int32_t *d_keys, int64_t n, int32_t 
         su.ready = true;
     }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    // The look-back words and ticket owners must start at zero.
-    if (cudaMemsetAsync(su.base + kOffPool, 0, kOffTask - kOffPool, s) != cudaSuccess)
+    // The look-back words, ticket owners and the control block (with its
+    // status words) start at zero: the previous call may have failed.
+    if (cudaMemsetAsync(su.base + kOffPool, 0, kBytes - kOffPool, s) != cudaSuccess)
         return fail(QS_ERR_CUDA, "cudaMemsetAsync failed");
 
     const KernelLimits lim = limits_i32();
@@ -110,7 +111,7 @@ extern "C" int64_t qs_partition_i32_noalloc(int32_t *d_keys, int64_t n, int32_t 
     a.leaf_cap = 1;
     a.leaf_max = lim.leaf_max;
     a.small_max = lim.small_max;
-    a.wait_limit_ns = 2000000000ull;
+    a.wait_limit_ns = option_wait_limit_ns();  // QS_OPT_WAIT_LIMIT_NS, as for qs_partition_i32
     a.pivot_bits = static_cast<uint64_t>(static_cast<int64_t>(pivot));
     a.partition_only = 1;
     a.ordered = 1;

@@ -12,10 +12,10 @@ generators", OOPSLA 2014): the state advances by the golden-ratio increment
 variant-13 mixing function (shifts 30, 27, 31 and two odd multipliers).
 
 Workload shapes follow the paper's experiments (random values, sizes
-2^1 .. 2^30, Section IV) and the five benchmark configurations described in
-the design doc: uniform / sorted / reverse / few-unique FP64, int32 key-value
-pairs with value = original index, batched uneven segments, and the skewed
-distributions used by the learned-splitter path.
+2^1 .. 2^30, Section IV) and the five benchmark configurations: uniform /
+sorted / reverse / few-unique FP64, int32 key-value pairs with value =
+original index, batched uneven segments, and the skewed distributions used
+by the learned-splitter path.
 """
 from __future__ import annotations
 

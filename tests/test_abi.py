@@ -53,9 +53,24 @@ def test_option_value_ranges(lib):
     assert lib.qs_set_option(opt["driver_ctas"], -1) == -1
     assert lib.qs_set_option(opt["driver_ctas"], (1 << 20) + 1) == -1
     assert lib.qs_set_option(opt["task_cap"], -1) == -1
-    for name in ("profile", "ordered", "driver_items", "leaf_max", "small_max", "driver_ctas", "task_cap"):
+    for v in (0, 1):
+        assert lib.qs_set_option(opt["sync"], v) == 0
+    for v in (-1, 2):
+        assert lib.qs_set_option(opt["sync"], v) == -1
+    for name in ("profile", "ordered", "driver_items", "leaf_max", "small_max", "driver_ctas", "task_cap", "sync"):
         assert lib.qs_set_option(opt[name], 0) == 0
     assert lib.qs_set_option(opt["wait_limit_ns"], 2_000_000_000) == 0
+
+
+def test_get_option_reads_back_what_was_set(lib):
+    for name, v in (("leaf_max", 1024), ("small_max", 64), ("driver_items", 8), ("sync", 1), ("ordered", 1)):
+        assert lib.qs_set_option(qs.OPTION[name], v) == 0
+        assert qs.get_option(name) == v
+        assert lib.qs_set_option(qs.OPTION[name], 0) == 0
+        assert qs.get_option(name) == 0
+    assert qs.get_option("wait_limit_ns") == 2_000_000_000
+    assert lib.qs_get_option(999, ctypes.byref(ctypes.c_int64())) == -1
+    assert lib.qs_get_option(qs.OPTION["sync"], None) == -1
 
 
 def test_option_names_match_header():

@@ -150,3 +150,79 @@ def test_segmented_full_workload():
     got = d.cpu().numpy()
     rng = np.random.default_rng(55)
     _check_segments(keys, got, offs, segs=[int(i) for i in rng.integers(0, 20_000, 40)])
+
+
+def test_segmented_full_workload_kv():
+    """The key/value variant of the 20,000-segment workload (values = original
+    index): on the GPU, every segment's keys are sorted, every output value
+    points back to an input position of the same segment holding the same key,
+    and the values are a permutation; plus 40 sampled segments against the
+    oracle (keys bit-exact, equal-key runs as value multisets)."""
+    import torch
+
+    qs = qs_gpu()
+    keys, offs = synth.segments_i32(20_000)
+    n = keys.size
+    vals = np.arange(n, dtype=np.int32)
+    dk = torch.from_numpy(keys).to("cuda")
+    dv = torch.from_numpy(vals).to("cuda")
+    keys_in = dk.clone()
+    doffs = torch.from_numpy(offs).to("cuda")
+    seg_id = torch.repeat_interleave(torch.arange(20_000, device="cuda", dtype=torch.int32),
+                                     doffs[1:] - doffs[:-1])
+    qs.sort_segmented(dk, doffs, dv)
+    torch.cuda.synchronize()
+    assert bool(((dk[1:] >= dk[:-1]) | (seg_id[1:] != seg_id[:-1])).all()), "a segment's keys are not sorted"
+    v64 = dv.to(torch.int64)
+    assert bool(((v64 >= 0) & (v64 < n)).all())
+    assert bool((keys_in[v64] == dk).all()), "a value does not point at its key"
+    assert bool((seg_id[v64] == seg_id).all()), "a value left its segment"
+    seen = torch.zeros(n, dtype=torch.int32, device="cuda").index_add_(0, v64, torch.ones_like(dv))
+    assert bool((seen == 1).all()), "values are not a permutation"
+    del seen, v64, keys_in, seg_id
+    gk, gv = dk.cpu().numpy(), dv.cpu().numpy()
+    rng = np.random.default_rng(56)
+    _check_segments(keys, gk, offs, segs=[int(i) for i in rng.integers(0, 20_000, 40)], vals_in=vals, vals_out=gv)
+
+
+@pytest.mark.parametrize("kind", ["i32", "kv"])
+def test_autotune_applies_caches_and_sorts_right(kind, tmp_path, monkeypatch):
+    """paper_1704_08579_gb300.autotune: the chosen leaf threshold, one-warp
+    threshold and tile variant come from the candidate lists, are applied
+    (read back with qs_get_option), are stored in the cache and returned from
+    it on the next call, and the segmented sort under them matches the oracle
+    per segment."""
+    import torch
+
+    from paper_1704_08579_gb300 import autotune
+
+    qs = qs_gpu()
+    monkeypatch.setattr(autotune, "CACHE_DIR", str(tmp_path))
+    offs = _segments(250, 57, hi=1 << 16)
+    n = int(offs[-1])
+    x = synth.uniform_i32(n, 58)
+    v = np.arange(n, dtype=np.int32) if kind == "kv" else None
+    dk, doffs = to_dev(x), to_dev(offs)
+    dv = to_dev(v) if v is not None else None
+    try:
+        res = autotune.tune(dk, doffs, dv, reps=1, use_cache=True)
+        assert res["leaf_max"] in autotune.LEAF_CHOICES[kind]
+        assert res["small_max"] in autotune.SMALL_CHOICES and res["small_max"] <= res["leaf_max"]
+        assert res["driver_items"] in autotune.ITEMS_CHOICES[kind]
+        assert len(res["table"]) >= 2 and res["ms"] == min(r["ms"] for r in res["table"])
+        for name in ("leaf_max", "small_max", "driver_items"):
+            assert qs.get_option(name) == res[name]
+        np.testing.assert_array_equal(dk.cpu().numpy(), x)  # tuning leaves the input alone
+        autotune.apply({})
+        again = autotune.tune(dk, doffs, dv, reps=1, use_cache=True)
+        assert again.get("cached") is True
+        for name in ("leaf_max", "small_max", "driver_items"):
+            assert again[name] == res[name] and qs.get_option(name) == res[name]
+        qs.sort_segmented(dk, doffs, dv)
+        torch.cuda.synchronize()
+        if v is None:
+            _check_segments(x, dk.cpu().numpy(), offs)
+        else:
+            _check_segments(x, dk.cpu().numpy(), offs, vals_in=v, vals_out=dv.cpu().numpy())
+    finally:
+        autotune.apply({})
