@@ -323,7 +323,7 @@ int qs_get_stats(qs_stats *out);
  *                        0 = all resident CTAs.
  *   QS_OPT_LEAF_MAX      parts of at most this many keys (a power of two,
  *                        >= 32) go to the Bitonic leaf kernel; 0 = the
- *                        compiled maximum (4096 f64/kv, 8192 i32), larger
+ *                        compiled maximum (16384 f64/kv, 32768 i32), larger
  *                        values are clamped to it.
  *   QS_OPT_SMALL_MAX     parts of at most this many keys (power of two, >= 32)
  *                        are sorted by one warp; 0 = the compiled maximum 512.

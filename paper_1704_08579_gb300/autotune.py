@@ -18,7 +18,7 @@ import paper_1704_08579_gb300 as qs
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_DIR = os.path.join(HERE, "tuning")
 
-LEAF_CHOICES = {"i32": (2048, 4096, 8192), "f64": (1024, 2048, 4096), "kv": (1024, 2048, 4096)}
+LEAF_CHOICES = {"i32": (8192, 16384, 32768), "f64": (4096, 8192, 16384), "kv": (4096, 8192, 16384)}
 SMALL_CHOICES = (128, 256, 512)
 ITEMS_CHOICES = {"i32": (16, 32), "f64": (16, 8), "kv": (16, 8)}  # the kind's default first
 

@@ -362,16 +362,17 @@ void stats_from_ctrl(const Workspace &w)
 // -- an earlier asynchronous call's (kept in the sticky word by the setup
 // kernel of the calls after it) or the last call's -- and clears it on the
 // device, so each failure is reported once.
-int report_status(Workspace &w, cudaStream_t s)
+int report_status(Workspace &w, cudaStream_t s, bool earlier_call = false)
 {
     static_assert(offsetof(Ctrl, sticky_info) == offsetof(Ctrl, status) + 3 * sizeof(int),
                   "status, info, sticky, sticky_info are contiguous");
     w.unreported = false;
     Ctrl &c = *w.h_ctrl;
-    const bool earlier = c.sticky != 0;
-    const int err = earlier ? c.sticky : c.status;
+    const bool sticky = c.sticky != 0;
+    const int err = sticky ? c.sticky : c.status;
     if (err == 0) return QS_OK;
-    const int info = earlier ? c.sticky_info : c.info;
+    const int info = sticky ? c.sticky_info : c.info;
+    const bool earlier = sticky || earlier_call;
     c.status = c.sticky = 0;
     w.dirty = true;  // look-back words and ticket owners are cleared before the next call
     cudaError_t e = cudaMemsetAsync(&w.ctrl->status, 0, 4 * sizeof(int), s);
@@ -393,7 +394,7 @@ int check_earlier(Workspace &w, cudaStream_t s)
     }
     if (q != cudaSuccess) return cuda_fail(q, "cudaEventQuery");
     stats_from_ctrl(w);
-    return report_status(w, s);
+    return report_status(w, s, true);
 }
 
 // Runs one sort (partition_only = 0) or partition (1) of kind `kind` on the

@@ -29,6 +29,7 @@ namespace qs {
 constexpr int kThreads = 256;            // threads per CTA in every kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kDThreads = 256;           // threads per CTA of the persistent partition kernel
+constexpr int kLThreads = 1024;          // threads per CTA of the leaf kernel (one CTA per SM)
 constexpr int kDWarps = kDThreads / 32;
 
 constexpr uint64_t kFlagAggregate = 1ull << 62;

@@ -10,15 +10,13 @@ namespace {
 // against 13.40 ms for the wide one at 3.  (FP64 and key/value sorts are
 // faster with the wide tile: 16.1 vs 17.0 ms and 16.9 vs 17.5 ms of
 // partition passes at 2^28.)
-using Tr = Traits<int32_t, false, 8, 8192, 512>;
-using TrN = Traits<int32_t, false, 4, 8192, 512>;
-// Minimum CTAs per SM: driver 3 (80 registers per thread; narrow tile 4 at
-// 64), leaf 4 (64
-// registers; the ALU-bound compare-exchange network hides its few spills --
-// FP64 leaf kernel at 2^28: 9.07 ms at 2 CTAs, 8.36 at 3, 7.96 at 4; int32
-// and key/value sorts equal at 3 and 4).
-using L = Launcher<Tr, 3 * 256 / kDThreads, 4>;
-using LN = Launcher<TrN, 4, 4>;
+using Tr = Traits<int32_t, false, 8, 32768, 512>;
+using TrN = Traits<int32_t, false, 4, 32768, 512>;
+// Minimum CTAs per SM of the persistent partition kernel: 3 (80 registers
+// per thread); the narrow int32 tile 4 (64 registers).  The leaf kernel
+// runs one 1024-thread CTA per SM.
+using L = Launcher<Tr, 3 * 256 / kDThreads>;
+using LN = Launcher<TrN, 4>;
 }  // namespace
 
 int launch_i32(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg)

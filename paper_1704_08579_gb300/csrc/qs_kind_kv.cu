@@ -6,14 +6,12 @@ namespace qs {
 namespace {
 // Two partition tile variants (items per thread); the wide one is the default,
 // the narrow one is chosen per call by QS_OPT_DRIVER_ITEMS (the autotuner).
-using Tr = Traits<int32_t, true, 4, 4096, 512>;
-using TrN = Traits<int32_t, true, 2, 4096, 512>;
-// Minimum CTAs per SM: driver 3 (80 registers per thread), leaf 4 (64
-// registers; the ALU-bound compare-exchange network hides its few spills --
-// FP64 leaf kernel at 2^28: 9.07 ms at 2 CTAs, 8.36 at 3, 7.96 at 4; int32
-// and key/value sorts equal at 3 and 4).
-using L = Launcher<Tr, 3 * 256 / kDThreads, 4>;
-using LN = Launcher<TrN, 3 * 256 / kDThreads, 4>;
+using Tr = Traits<int32_t, true, 4, 16384, 512>;
+using TrN = Traits<int32_t, true, 2, 16384, 512>;
+// Minimum CTAs per SM of the persistent partition kernel: 3 (80 registers
+// per thread).  The leaf kernel runs one 1024-thread CTA per SM.
+using L = Launcher<Tr, 3 * 256 / kDThreads>;
+using LN = Launcher<TrN, 3 * 256 / kDThreads>;
 }  // namespace
 
 int launch_kv(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg)

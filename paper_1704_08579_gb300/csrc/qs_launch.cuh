@@ -10,7 +10,7 @@
 
 namespace qs {
 
-template <class Tr, int DriverMin, int LeafMin>
+template <class Tr, int DriverMin>
 struct Launcher {
     using K = typename Tr::K;
     using V = typename Tr::V;
@@ -23,7 +23,7 @@ struct Launcher {
         l.small_max = Tr::SMALL;
         l.tile = Tr::T;
         l.driver_smem = kDriverSmem;
-        l.leaf_smem = sizeof(LeafSmem<Tr>);
+        l.leaf_smem = sizeof(LeafSmem<Tr>) + LeafCfg<Tr>::kDynSmem;
         return l;
     }
     static int prepare()
@@ -33,6 +33,9 @@ struct Launcher {
         if (!done) {
             rc = cudaFuncSetAttribute(driver_kernel<Tr, DriverMin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(kDriverSmem));
+            if (rc == 0)
+                rc = cudaFuncSetAttribute(leaf_kernel<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(LeafCfg<Tr>::kDynSmem));
             done = 1;
         }
         return rc;
@@ -44,7 +47,7 @@ struct Launcher {
         if (which == 0)
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, driver_kernel<Tr, DriverMin>, kDThreads,
                                                                  kDriverSmem);
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, leaf_kernel<Tr, LeafMin>, kThreads, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, leaf_kernel<Tr>, kLThreads, LeafCfg<Tr>::kDynSmem);
     }
     static int launch(const Args<K, V> &a, LaunchCfg &cfg)
     {
@@ -62,7 +65,7 @@ struct Launcher {
         if (a.partition_only || a.seg_off || a.n > a.leaf_max)
             driver_kernel<Tr, DriverMin><<<cfg.grid_driver, kDThreads, kDriverSmem, s>>>(a);
         if (cfg.profile) cudaEventRecord(ev[2], s);
-        if (!a.partition_only) leaf_kernel<Tr, LeafMin><<<cfg.grid_leaf, kThreads, 0, s>>>(a);
+        if (!a.partition_only) leaf_kernel<Tr><<<cfg.grid_leaf, kLThreads, LeafCfg<Tr>::kDynSmem, s>>>(a);
         if (cfg.profile) cudaEventRecord(ev[3], s);
         return static_cast<int>(cudaGetLastError());
     }

@@ -1,15 +1,18 @@
-// Leaf kernel: every part listed by the partition driver is sorted with the
-// Bitonic network (Section III-A) into the caller's array, or -- for a
-// finished run of equal keys -- copied back from scratch.  Parts larger than
-// SMALL keys take one CTA each (registers + shuffles + shared memory); parts
-// of at most SMALL keys take one warp each (registers + shuffles only).  The
-// tail of a part is padded with the largest sort-space key (Section III-A-3).
+// Leaf kernel: every part listed by the partition driver is sorted into the
+// caller's array, or -- for a finished run of equal keys -- copied back from
+// scratch.  Parts larger than SMALL keys take a group of 32*m threads of a
+// 1024-thread CTA (one CTA per SM, the part in shared memory): Bitonic runs
+// in registers merged by merge path (qs_merge.cuh); several parts share a
+// CTA.  Parts of at most SMALL keys take one warp each and the Bitonic
+// network alone (registers + shuffles).  The tail of a part is padded with
+// the largest sort-space key (Section III-A-3).
 #pragma once
 
 #include <type_traits>
 
 #include "qs_bitonic.cuh"
 #include "qs_common.cuh"
+#include "qs_merge.cuh"
 
 namespace qs {
 
@@ -48,26 +51,29 @@ struct LeafKey {
     }
 };
 
-// Registers per thread of the group network: 16 for 64-bit sort keys, 32 for
-// 32-bit ones, so a CTA of kThreads threads holds Tr::LEAF keys.
+// Keys per thread of a group: 16 for 64-bit sort keys, 32 for 32-bit ones
+// (one 128-byte run each), so a CTA of kLThreads threads holds Tr::LEAF keys.
 template <class Tr>
 struct LeafCfg {
     using S = typename LeafKey<Tr>::S;
     static constexpr int E = sizeof(S) == 8 ? 16 : 32;
-    static constexpr int LE = sizeof(S) == 8 ? 4 : 5;
-    static_assert(kThreads * E == Tr::LEAF, "a CTA holds exactly one largest leaf");
+    static_assert(kLThreads * E == Tr::LEAF, "a CTA holds exactly one largest leaf");
+    static constexpr size_t kDynSmem = sizeof(S) * Tr::LEAF;  // the keys, in dynamic shared memory
 };
 
 struct LeafGroup {
     Leaf leaf;
     int start;     // first thread of the group
-    int nthreads;  // 32 .. kThreads
+    int nthreads;  // 32 .. kLThreads, a multiple of 32
+    int bar;       // named barrier of the group (groups of one warp use __syncwarp)
 };
+
+// Named barriers 1..15 are available to groups (barrier 0 is __syncthreads).
+constexpr int kLeafBarriers = 15;
 
 template <class Tr>
 struct LeafSmem {
-    typename LeafKey<Tr>::S keys[Tr::LEAF + Tr::LEAF / 16];
-    LeafGroup grp[kThreads / 32];
+    LeafGroup grp[kLThreads / 32];
     Leaf carry;
     int has_carry;
     int ngroups;
@@ -85,64 +91,47 @@ __device__ bool leaf_ok(const Args<typename Tr::K, typename Tr::V> &a, const Lea
 }
 
 // Sorts one leaf with a group of `nthreads` threads starting at thread
-// `start`; the group owns the shared-memory slice of its threads.
+// `start`; the group owns the slice of shared memory of its threads' runs.
 template <class Tr>
-__device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l, LeafSmem<Tr> &sm, int start,
-                           int nthreads, int bar)
+__device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l,
+                           typename LeafKey<Tr>::S *keys, int start, int nthreads, int bar)
 {
     using LK = LeafKey<Tr>;
     using S = typename LK::S;
-    constexpr int E = LeafCfg<Tr>::E, LE = LeafCfg<Tr>::LE;
-    S *gs = sm.keys + padk<S>(start * E);
+    constexpr int E = LeafCfg<Tr>::E;
+    S *gs = keys + start * E;
     const int g = threadIdx.x - start;
-    const int P = nthreads * E;
-    const int L = __ffs(P) - 1;
     const int src = (l.flags & kLeafScratch) ? 1 : 0;
     const typename Tr::K *gk = a.keys[src] + l.off;
     const typename Tr::V *gv = a.vals[src] + l.off;
     const int len = l.len;
     long long t0 = (a.profile && g == 0) ? prof_clock() : 0;
-    // Coalesced load, tail padded with the largest key: all E loads of a
-    // thread are issued before the first one is used.
-    {
-        S t[E];
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const int i = g + r * nthreads;
-            t[r] = i < len ? LK::load(gk, gv, i) : LK::largest();
-        }
-#pragma unroll
-        for (int r = 0; r < E; ++r) gs[padk<S>(g + r * nthreads)] = t[r];
-    }
-    group_sync(bar, nthreads);
+    // Coalesced loads across the group, tail padded with the largest key.
     S k[E];
-    lay_load<E, LE, S>(k, gs, g, 0);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int i = g + r * nthreads;
+        k[r] = i < len ? LK::load(gk, gv, i) : LK::largest();
+    }
     if (a.profile && g == 0) {
         const long long t = prof_clock();
         atomicAdd(&a.ctrl->cycles[20], static_cast<unsigned long long>(t - t0));
         t0 = t;
     }
-    switch (L - LE) {  // log2 of the group's threads: 32 .. kThreads
-    case 5: group_bitonic_sort<E, LE, LE + 5, S>(k, gs, g, bar, nthreads); break;
-    case 6: group_bitonic_sort<E, LE, LE + 6, S>(k, gs, g, bar, nthreads); break;
-    case 7: group_bitonic_sort<E, LE, LE + 7, S>(k, gs, g, bar, nthreads); break;
-    default: group_bitonic_sort<E, LE, LE + 8, S>(k, gs, g, bar, nthreads); break;
-    }
+    group_merge_sort<E, S>(k, gs, g, nthreads, bar, LK::largest());
     if (a.profile && g == 0) {
         const long long t = prof_clock();
         atomicAdd(&a.ctrl->cycles[21], static_cast<unsigned long long>(t - t0));
-        atomicAdd(&a.ctrl->cycles[22], static_cast<unsigned long long>(P - len));  // padding slots
+        atomicAdd(&a.ctrl->cycles[22], static_cast<unsigned long long>(nthreads * E - len));  // padding slots
         t0 = t;
     }
-    group_sync(bar, nthreads);
-    lay_store<E, LE, S>(k, gs, g, 0);
     group_sync(bar, nthreads);
     typename Tr::K *ok = a.keys[0] + l.off;
     typename Tr::V *ov = a.vals[0] + l.off;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int i = g + r * nthreads;
-        if (i < len) LK::store(ok, ov, i, gs[padk<S>(i)]);
+        if (i < len) LK::store(ok, ov, i, gs[swz<E>(i)]);
     }
     if (a.profile && g == 0) atomicAdd(&a.ctrl->cycles[23], static_cast<unsigned long long>(prof_clock() - t0));
 }
@@ -173,12 +162,15 @@ __device__ void warp_leaf(const Args<typename Tr::K, typename Tr::V> &a, const L
     }
 }
 
-template <class Tr, int MinBlocks>
-__global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename Tr::K, typename Tr::V> a)
+template <class Tr>
+__global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K, typename Tr::V> a)
 {
     using K = typename Tr::K;
     using V = typename Tr::V;
+    using S = typename LeafKey<Tr>::S;
     __shared__ LeafSmem<Tr> sm;
+    extern __shared__ __align__(128) unsigned char leaf_dyn[];
+    S *keys = reinterpret_cast<S *>(leaf_dyn);
     Ctrl *c = a.ctrl;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) sm.idx = ld_relaxed_s32(&c->status);
@@ -190,8 +182,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
         // before the host has seen this error -- starts from a clean state.
         unsigned long long used = ld_relaxed_u64(&c->pool_cursor);
         if (used > static_cast<unsigned long long>(a.pool_cap)) used = static_cast<unsigned long long>(a.pool_cap);
-        const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * kThreads;
-        for (unsigned long long i = static_cast<unsigned long long>(blockIdx.x) * kThreads + tid; i < used; i += stride) {
+        const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * kLThreads;
+        for (unsigned long long i = static_cast<unsigned long long>(blockIdx.x) * kLThreads + tid; i < used; i += stride) {
             a.pool[i] = 0;
             a.owner[i] = 0;
         }
@@ -202,13 +194,14 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
     const long long n_small = static_cast<long long>(ld_relaxed_u64(&c->n_small));
     constexpr int E = LeafCfg<Tr>::E;
     if (tid == 0) sm.has_carry = 0;
-    // Large parts: thread 0 packs parts into thread groups (32 .. kThreads
-    // threads each, E keys per thread); a part that does not fit is carried
-    // over to this CTA's next pass.
+    // Large parts: thread 0 packs parts into thread groups (32 .. kLThreads
+    // threads each, a multiple of 32, E keys per thread); a part that does
+    // not fit (or finds no named barrier left) is carried over to this CTA's
+    // next pass.
     for (;;) {
         const long long tp = (a.profile && tid == 0) ? prof_clock() : 0;
         if (tid == 0) {
-            int ng = 0, used = 0;
+            int ng = 0, used = 0, nbar = 0;
             for (;;) {
                 Leaf l;
                 if (sm.has_carry) {
@@ -220,12 +213,9 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
                     l = a.leaves[idx];
                     if (!leaf_ok<Tr>(a, l, false)) continue;
                 }
-                int need = kThreads;
-                if (!(l.flags & kLeafFinal)) {
-                    need = 32;
-                    while (need * E < l.len) need *= 2;
-                }
-                if (used + need > kThreads) {
+                int need = kLThreads;
+                if (!(l.flags & kLeafFinal)) need = 32 * ((l.len + 32 * E - 1) / (32 * E));
+                if (used + need > kLThreads || (need > 32 && nbar == kLeafBarriers)) {
                     sm.carry = l;
                     sm.has_carry = 1;
                     break;
@@ -233,9 +223,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
                 sm.grp[ng].leaf = l;
                 sm.grp[ng].start = used;
                 sm.grp[ng].nthreads = need;
+                sm.grp[ng].bar = need > 32 ? ++nbar : 0;
                 ++ng;
                 used += need;
-                if (used == kThreads) break;
+                if (used == kLThreads) break;
             }
             sm.ngroups = ng;
             if (a.profile) atomicAdd(&a.ctrl->cycles[19], static_cast<unsigned long long>(prof_clock() - tp));
@@ -251,12 +242,12 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
             if (l.flags & kLeafFinal) {
                 const K *gk = a.keys[1] + l.off;
                 const V *gv = a.vals[1] + l.off;
-                for (int i = tid; i < l.len; i += kThreads) {
+                for (int i = tid; i < l.len; i += kLThreads) {
                     a.keys[0][l.off + i] = gk[i];
                     if constexpr (Tr::KV) a.vals[0][l.off + i] = gv[i];
                 }
             } else {
-                group_leaf<Tr>(a, l, sm, sm.grp[gi].start, sm.grp[gi].nthreads, gi + 1);
+                group_leaf<Tr>(a, l, keys, sm.grp[gi].start, sm.grp[gi].nthreads, sm.grp[gi].bar);
             }
         }
         __syncthreads();
@@ -264,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) leaf_kernel(Args<typename
     // Small parts: one warp each, claimed in batches of up to 32 when there
     // are many (one atomic and one coalesced read of the descriptors per
     // batch), one at a time when there are few (so every warp gets work).
-    const long long nwarps_all = static_cast<long long>(gridDim.x) * (kThreads / 32);
+    const long long nwarps_all = static_cast<long long>(gridDim.x) * (kLThreads / 32);
     const long long per_warp = n_small / (8 * nwarps_all);
     const int batch = per_warp >= 32 ? 32 : (per_warp < 1 ? 1 : static_cast<int>(per_warp));
     for (;;) {

@@ -160,6 +160,7 @@ def test_async_timeout_reported_and_recovers():
     x = synth.uniform_f64(1 << 20, 670)
     y = synth.uniform_f64(700_001, 671)
     d, dy = to_dev(x), to_dev(y)
+    qs.reserve(1 << 20, "f64")  # no workspace growth (cudaFree synchronises) inside the two calls
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         torch.cuda._sleep(100_000_000)  # holds the stream, so both sorts are enqueued before either runs

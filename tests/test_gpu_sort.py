@@ -2,8 +2,9 @@
 III-A..III-D).  Keys must be bit-identical to the oracle's; for key/value
 pairs each run of equal keys must hold the same multiset of values.
 
-Sizes cover the single-warp leaf (<= 512), the CTA leaf (<= 8192 i32,
-<= 4096 f64/kv), several device-wide partition levels, ragged tails,
+Sizes cover the single-warp leaf (<= 512), the merge-path group leaf (<= 32768
+i32, <= 16384 f64/kv; groups of any multiple of 32 threads, so run counts that
+are not powers of two), several device-wide partition levels, ragged tails,
 duplicate-heavy and all-equal inputs, extreme keys and unaligned pointers.
 """
 import numpy as np
@@ -14,8 +15,8 @@ from qs_testutil import assert_keys_equal, assert_kv_sorted_equal, oracle_sort, 
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [2, 3, 31, 32, 33, 100, 511, 512, 513, 1000, 2049, 4095, 4096, 4097, 8191, 8192, 8193, 12_345,
-         65_543, 300_001]
+SIZES = [2, 3, 31, 32, 33, 100, 511, 512, 513, 1000, 1025, 1536, 2049, 3000, 4095, 4096, 4097, 7_000, 8191, 8192,
+         8193, 12_345, 16_383, 16_384, 16_385, 23_457, 32_767, 32_768, 32_769, 65_543, 300_001]
 
 
 def _sort_dev(qs, x, v=None, koff=0, voff=0):
@@ -281,7 +282,7 @@ def test_small_leaf_thresholds(kind):
     of equal keys)."""
     qs = qs_gpu()
     try:
-        for leaf, small in ((32, 32), (64, 32), (512, 64), (2048, 256)):
+        for leaf, small in ((32, 32), (64, 32), (512, 64), (2048, 256), (8192, 512)):
             qs.set_option("leaf_max", leaf)
             qs.set_option("small_max", small)
             for ordered in (0, 1):
