@@ -68,18 +68,26 @@ __device__ __forceinline__ void reg_merges(S (&k)[E])
     }
 }
 
-// Flip stage across lanes: lane l pairs with l ^ lm, register r with E-1-r.
-// `upper` is true on the lane holding the higher indices (keeps the maximum).
+// Flip stage across lanes: lane l pairs register r with register E-1-r of
+// lane l ^ lm.  `upper` is true on the lane holding the higher indices (keeps
+// the maximum).  Registers r and E-1-r are exchanged together, so no
+// temporary array of E partner values is needed.
 template <int E, class S>
 __device__ __forceinline__ void shfl_flip(S (&k)[E], int lm, bool upper)
 {
-    S o[E];
 #pragma unroll
-    for (int r = 0; r < E; ++r) o[r] = __shfl_xor_sync(0xffffffffu, k[E - 1 - r], lm);
-#pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const bool take = upper ? (k[r] < o[r]) : (o[r] < k[r]);
-        k[r] = take ? o[r] : k[r];
+    for (int r = 0; r < E / 2; ++r) {
+        const S o_lo = __shfl_xor_sync(0xffffffffu, k[E - 1 - r], lm);
+        const S o_hi = __shfl_xor_sync(0xffffffffu, k[r], lm);
+        const bool t0 = upper ? (k[r] < o_lo) : (o_lo < k[r]);
+        const bool t1 = upper ? (k[E - 1 - r] < o_hi) : (o_hi < k[E - 1 - r]);
+        k[r] = t0 ? o_lo : k[r];
+        k[E - 1 - r] = t1 ? o_hi : k[E - 1 - r];
+    }
+    if constexpr (E == 1) {
+        const S o = __shfl_xor_sync(0xffffffffu, k[0], lm);
+        const bool t = upper ? (k[0] < o) : (o < k[0]);
+        k[0] = t ? o : k[0];
     }
 }
 

@@ -118,7 +118,7 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
         atomicAdd(&a.ctrl->cycles[20], static_cast<unsigned long long>(t - t0));
         t0 = t;
     }
-    group_merge_sort<E, S>(k, gs, g, nthreads, bar, LK::largest());
+    group_merge_sort<E, S>(k, gs, g, nthreads, bar);
     if (a.profile && g == 0) {
         const long long t = prof_clock();
         atomicAdd(&a.ctrl->cycles[21], static_cast<unsigned long long>(t - t0));
