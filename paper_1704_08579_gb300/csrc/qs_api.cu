@@ -70,6 +70,7 @@ struct Workspace {
     Ctrl *ctrl = nullptr;
     Ctrl *h_ctrl = nullptr;
     bool dirty = true;  // look-back words / ticket owners must be cleared before use
+    int64_t dirty_words = 0;  // else: the first dirty_words of them (left by a partition-only call)
     cudaEvent_t ev[6] = {};
     // Ordering of calls on this workspace: every call waits (on its own
     // stream) for `done`, recorded after the previous call's last operation,
@@ -324,6 +325,22 @@ Args<K, int32_t> make_args(Workspace &w, int kind, K *keys, int32_t *vals, int64
     return a;
 }
 
+// Clears the look-back words and ticket owners a previous call left set.
+cudaError_t clear_dirty(Workspace &w, cudaStream_t s)
+{
+    const int64_t words = w.dirty ? w.pool_cap : (w.dirty_words < w.pool_cap ? w.dirty_words : w.pool_cap);
+    cudaError_t e = cudaSuccess;
+    if (words > 0) {
+        e = cudaMemsetAsync(w.pool, 0, static_cast<size_t>(words) * 8, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.owner, 0, static_cast<size_t>(words) * 4, s);
+    }
+    if (e == cudaSuccess) {
+        w.dirty = false;
+        w.dirty_words = 0;
+    }
+    return e;
+}
+
 // Ordering of the calls that share a workspace: `s` waits for the last
 // operation of the previous call, whatever stream it was issued on.
 cudaError_t order_after_previous(Workspace &w, cudaStream_t s)
@@ -435,13 +452,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if ((rc = check_earlier(w, s))) return rc;
     if ((e = order_after_previous(w, s)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
-    if (w.dirty) {
-        if ((e = cudaMemsetAsync(w.pool, 0, static_cast<size_t>(w.pool_cap) * 8, s)) != cudaSuccess)
-            return cuda_fail(e, "cudaMemsetAsync");
-        if ((e = cudaMemsetAsync(w.owner, 0, static_cast<size_t>(w.pool_cap) * 4, s)) != cudaSuccess)
-            return cuda_fail(e, "cudaMemsetAsync");
-        w.dirty = false;
-    }
+    if ((e = clear_dirty(w, s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     Args<K, int32_t> a = make_args<K>(w, kind, keys, vals, n);
     a.pivot_bits = pivot_bits;
     a.partition_only = partition_only;
@@ -522,6 +533,8 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     const unsigned long long lt = w.h_ctrl->lt_result;
     if ((rc = report_status(w, s))) return rc;
     if (partition_only) {
+        // Its CTAs left without clearing the look-back words they used.
+        w.dirty_words = static_cast<int64_t>(w.h_ctrl->pool_cursor);
         // The split is known; move the partitioned data back into the caller's arrays.
         if (cfg.profile) cudaEventRecord(w.ev[4], s);
         if ((e = cudaMemcpyAsync(keys, w.scratch_k, static_cast<size_t>(n) * sizeof(K), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
@@ -656,12 +669,7 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if ((rc = check_earlier(w, s))) return rc;
     if ((e = order_after_previous(w, s)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
-    if (w.dirty) {
-        if ((e = cudaMemsetAsync(w.pool, 0, static_cast<size_t>(w.pool_cap) * 8, s)) != cudaSuccess ||
-            (e = cudaMemsetAsync(w.owner, 0, static_cast<size_t>(w.pool_cap) * 4, s)) != cudaSuccess)
-            return cuda_fail(e, "cudaMemsetAsync");
-        w.dirty = false;
-    }
+    if ((e = clear_dirty(w, s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     Args<K, int32_t> a = make_args<K>(w, kind, keys, nullptr, n);
     LearnedCall lc;
     std::memset(&lc, 0, sizeof(lc));

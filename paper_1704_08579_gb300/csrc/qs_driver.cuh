@@ -376,6 +376,13 @@ __device__ WorkItem resolve_blocking(const Args<typename Tr::K, typename Tr::V> 
     Ctrl *c = a.ctrl;
     uint64_t t0 = 0;
     unsigned ns = 32;
+    if (a.partition_only && g >= __ldcg(&a.tasks[0].ntiles)) {
+        // A partition-only call has one task, published before the kernel
+        // starts: a ticket past its tiles means there is no work left.
+        WorkItem w = hint;
+        w.kind = 0;
+        return w;
+    }
     for (;;) {
         WorkItem w = try_resolve<Tr>(a, g, hint);
         if (w.kind == 1 || ld_relaxed_s32(&c->status) != 0) {
@@ -758,6 +765,8 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
                 sm.abort = excl < 0;
                 if (excl >= 0 && w.tile == w.ntiles - 1)
                     st_relaxed_u64(&a.tasks[w.task].lt_total, static_cast<unsigned long long>(excl + total));
+                if (excl >= 0 && w.tile == w.ntiles - 1 && a.partition_only)
+                    a.ctrl->lt_result = static_cast<unsigned long long>(excl + total);  // the split
             }
             const long long tst = a.profile ? prof_clock() : 0;
             stage(total);
@@ -864,7 +873,10 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         sm.wp = w;
         sm.prev_eq = sm.eq_total;
         sm.eq_total = 0;
-        sm.has_prev = 1;
+        // A partition-only call completes no task (its split is recorded by
+        // its last tile, its CTAs leave when the tickets run out), so its
+        // tiles need no release.
+        sm.has_prev = a.partition_only ? 0 : 1;
     }
     __syncthreads();
 #undef QS_TICK
@@ -1129,7 +1141,9 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
     if (aborted) return;
     // Clean exit: every task is finished, so no CTA reads the look-back words
     // or the ticket owners any more; clear this CTA's share for the next call.
-    if (ld_relaxed_s32(&a.ctrl->status) == 0) {
+    // (A partition-only call's CTAs leave while others may still read the
+    // look-back words; the host clears the words it used before the next call.)
+    if (!a.partition_only && ld_relaxed_s32(&a.ctrl->status) == 0) {
         const unsigned long long used = ld_relaxed_u64(&a.ctrl->pool_cursor);
         const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * kDThreads;
         for (unsigned long long i = blockIdx.x * kDThreads + tid; i < used; i += stride) {

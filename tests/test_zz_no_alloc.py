@@ -98,20 +98,26 @@ def test_noalloc_agrees_with_regular_entry_point():
 
 def test_noalloc_honours_the_wait_limit_and_recovers():
     """QS_OPT_WAIT_LIMIT_NS applies here as for qs_partition_i32: with a limit
-    of 0 the persistent kernel's waits run out (QS_ERR_TIMEOUT, reported
-    without a hang), and the next call is right again."""
+    of 0 any wait of the persistent kernel (a tile's bulk copy, the
+    look-back) that does not succeed at once ends the call with QS_ERR_TIMEOUT
+    instead of hanging -- whether one happens depends on timing, so a call
+    either reports the timeout or returns the right split -- and the next call
+    with the normal limit is right again."""
     qs = qs_gpu()
     lib = qs.load()
     x = synth.uniform_i32(MAX_N, 940)
     pivot = x[5]
+    exp_split, exp = oracle_partition(x, pivot)
     qs.set_option("wait_limit_ns", 0)
     try:
-        split, _ = _noalloc(lib, x, pivot, _stream())
+        results = [_noalloc(lib, x, pivot, _stream()) for _ in range(5)]
     finally:
         qs.set_option("wait_limit_ns", 2_000_000_000)
-    assert split == -5
+    for split, got in results:
+        assert split in (-5, exp_split)
+        if split == exp_split:
+            assert_keys_equal(got, exp)
     split, got = _noalloc(lib, x, pivot, _stream())
-    exp_split, exp = oracle_partition(x, pivot)
     assert split == exp_split
     assert_keys_equal(got, exp)
 
