@@ -329,9 +329,12 @@ int qs_get_stats(qs_stats *out);
  *                        are sorted by one warp; 0 = the compiled maximum 512.
  *   QS_OPT_DRIVER_ITEMS  keys per thread of a partition tile: each kind has a
  *                        wide and a narrow compiled variant (i32 32 / 16,
- *                        f64 16 / 8, kv 16 / 8); the narrow value selects the
- *                        narrow one, 0 the kind's default (i32 narrow, f64
- *                        and kv wide), any other value the wide one.
+ *                        f64 16 / 8, kv 16 / 8), and f64 and kv a register
+ *                        tile of 32 keys per thread (64 KB, loaded straight
+ *                        into registers, no prefetch buffer, 2 CTAs per SM);
+ *                        the narrow or register-tile value selects that
+ *                        variant, 0 the kind's default (i32 narrow, f64 and
+ *                        kv wide), any other value the wide one.
  *   QS_OPT_ORDERED       0 (default): inside a sort, each partition tile
  *                        claims its lower- and upper-side output ranges with
  *                        one atomic add each on its task's two counters, so

@@ -1,7 +1,7 @@
 """Autotuner for the run-time knobs of the sort: the leaf threshold (largest
 part handed to the Bitonic kernel, QS_OPT_LEAF_MAX), the one-warp threshold
 (QS_OPT_SMALL_MAX) and the keys per thread of a partition tile
-(QS_OPT_DRIVER_ITEMS, one of the two compiled tile variants).  Each candidate
+(QS_OPT_DRIVER_ITEMS, one of the compiled tile variants).  Each candidate
 is timed on the caller's own data with CUDA events (a fresh copy of the input
 per run, so every run sorts the same unsorted data); the fastest is kept,
 applied with qs_set_option, and recorded in a JSON cache keyed by GPU name and
@@ -20,7 +20,7 @@ CACHE_DIR = os.path.join(HERE, "tuning")
 
 LEAF_CHOICES = {"i32": (8192, 16384, 32768), "f64": (4096, 8192, 16384), "kv": (4096, 8192, 16384)}
 SMALL_CHOICES = (128, 256, 512)
-ITEMS_CHOICES = {"i32": (16, 32), "f64": (16, 8), "kv": (16, 8)}  # the kind's default first
+ITEMS_CHOICES = {"i32": (16, 32), "f64": (16, 8, 32), "kv": (16, 8, 32)}  # the kind's default first
 
 
 def _cache_path(gpu_name: str) -> str:

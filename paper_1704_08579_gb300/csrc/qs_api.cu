@@ -55,7 +55,7 @@ struct Workspace {
     std::mutex mu;
     bool init = false;
     int sms = 0;
-    int occ[3][3] = {};  // per kind: driver (wide tile), leaf, driver (narrow tile)
+    int occ[3][4] = {};  // per kind: driver (wide tile), leaf, driver (narrow tile), driver (register tile)
     void *scratch_k = nullptr, *scratch_v = nullptr;
     size_t scratch_k_bytes = 0, scratch_v_bytes = 0;
     void *stage_k = nullptr, *stage_v = nullptr;
@@ -148,7 +148,7 @@ int ws_init(Workspace &w)
     e = cudaDeviceGetAttribute(&w.sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     for (int k = 0; k < 3; ++k)
-        for (int which = 0; which < 3; ++which) {
+        for (int which = 0; which < 4; ++which) {
             e = static_cast<cudaError_t>(occupancy_of(k, which, &w.occ[k][which]));
             if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
             if (w.occ[k][which] < 1) return fail(QS_ERR_INTERNAL, "kernel cannot be resident (kind %d)", k);
@@ -173,6 +173,14 @@ struct Needs {
     size_t key_bytes, val_bytes;
     int64_t task_cap, pool_cap, leaf_cap;
 };
+
+// Occupancy slot of the partition tile variant selected by `items` (keys per thread).
+int tile_variant(int kind, int items)
+{
+    const KernelLimits l = limits_of(kind);
+    if (l.items_xwide && items == l.items_xwide) return 3;
+    return items == l.items_narrow ? 2 : 0;
+}
 
 int64_t leaf_max_of(int kind)
 {
@@ -466,8 +474,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     const int64_t ctas = g_driver_ctas.load();
     cfg.items = static_cast<int>(g_driver_items.load());
     if (cfg.items == 0) cfg.items = limits_of(kind).items_default;
-    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas)
-                               : w.sms * w.occ[kind][cfg.items == limits_of(kind).items_narrow ? 2 : 0];
+    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][tile_variant(kind, cfg.items)];
     cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];
     cfg.profile = g_profile.load();
     for (int i = 0; i < 6; ++i) cfg.ev[i] = w.ev[i];
@@ -689,8 +696,7 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     const int64_t ctas = g_driver_ctas.load();
     cfg.items = static_cast<int>(g_driver_items.load());
     if (cfg.items == 0) cfg.items = limits_of(kind).items_default;
-    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas)
-                               : w.sms * w.occ[kind][cfg.items == limits_of(kind).items_narrow ? 2 : 0];
+    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][tile_variant(kind, cfg.items)];
     cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];
     cfg.profile = g_profile.load();
     for (int i = 0; i < 6; ++i) cfg.ev[i] = w.ev[i];

@@ -103,7 +103,11 @@ __device__ __forceinline__ bool goes_low(typename Ops::Raw k, typename Ops::Raw 
 //   T     keys per partition tile
 //   LEAF  largest part handed to the Bitonic kernel (power of two)
 //   SMALL largest part sorted by a single warp (power of two)
-template <class K_, bool KV_, int VPT_, int LEAF_, int SMALL_>
+//   PF    true: the next tile is prefetched into a second shared-memory
+//         buffer by a TMA bulk copy; false: a tile is loaded straight into
+//         registers with 16-byte loads (one shared-memory buffer, for
+//         staging only), for tiles too large to double-buffer
+template <class K_, bool KV_, int VPT_, int LEAF_, int SMALL_, bool PF_ = true>
 struct Traits {
     using K = K_;
     using V = int32_t;
@@ -115,6 +119,8 @@ struct Traits {
     static constexpr int T = kDThreads * E;  // keys per partition tile
     static constexpr int LEAF = LEAF_;
     static constexpr int SMALL = SMALL_;
+    static constexpr bool PF = PF_;
+    static constexpr int NBUF = PF_ ? 2 : 1;  // shared-memory tile buffers
     static_assert(E <= 32, "per-thread flags are kept in one 32-bit mask");
 };
 

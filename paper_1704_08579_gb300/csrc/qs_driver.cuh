@@ -273,8 +273,8 @@ constexpr int kCountThreads = kDThreads - 64;
 
 template <class Tr>
 struct DriverSmem {
-    alignas(128) typename Tr::K kbuf[2][Tr::T];
-    alignas(128) typename Tr::V vbuf[2][Tr::KV ? Tr::T : 4];
+    alignas(128) typename Tr::K kbuf[Tr::NBUF][Tr::T];
+    alignas(128) typename Tr::V vbuf[Tr::NBUF][Tr::KV ? Tr::T : 4];
     alignas(8) unsigned long long bar[2];
     int wcount[Tr::VPT * kDWarps];
     long long excl;
@@ -312,7 +312,7 @@ template <class Tr>
 __device__ __forceinline__ void issue_tile_load(const Args<typename Tr::K, typename Tr::V> &a, const WorkItem &w,
                                                 DriverSmem<Tr> &sm, int b)
 {
-    if (!w.full) return;
+    if (!Tr::PF || !w.full) return;
     const int64_t base = w.w0 + static_cast<int64_t>(w.tile) * Tr::T;
     constexpr uint32_t kb = Tr::T * sizeof(typename Tr::K);
     constexpr uint32_t vb = Tr::KV ? Tr::T * sizeof(typename Tr::V) : 0;
@@ -628,7 +628,28 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     // whole CTA has consumed the phase; on abort it stays, so the exit drain
     // waits for the very copy that was late.
     bool landed = true;
-    if (w.full) {
+    if (!Tr::PF && w.full) {
+        // Register tile: 16-byte loads straight from global memory, coalesced
+        // across the CTA (the tile's start is 16-byte aligned, see fill_tile).
+        const Vec *gk = reinterpret_cast<const Vec *>(a.keys[w.src] + base);
+        const int4 *gv = reinterpret_cast<const int4 *>(a.vals[w.src] + base);
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+            K tmp[VW];
+            Ops::split(__ldcg(gk + k * kDThreads + tid), tmp);
+#pragma unroll
+            for (int j = 0; j < VW; ++j) key[k * VW + j] = tmp[j];
+            if constexpr (Tr::KV) {
+                const int4 vv = __ldcg(gv + k * kDThreads + tid);
+                val[k * VW + 0] = vv.x;
+                val[k * VW + 1] = vv.y;
+                val[k * VW + 2] = vv.z;
+                val[k * VW + 3] = vv.w;
+            }
+        }
+        validm = E == 32 ? 0xffffffffu : ((1u << E) - 1u);
+        QS_TICK(1);
+    } else if (w.full) {
         landed = mbar_wait_bounded(&sm.bar[b], (phases >> b) & 1u, a.ctrl, a.wait_limit_ns);
         QS_TICK(1);
         const Vec *sv = reinterpret_cast<const Vec *>(sm.kbuf[b]);
@@ -691,7 +712,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     if (lane == 0 && eq) atomicAdd(&sm.eq_total, eq);
     if (a.profile && tid == 0) sm.tm[18] += prof_clock() - tprev;  // own work, before the barrier
     if (__syncthreads_or(landed ? 0 : 1)) return -1;  // CTA-uniform: some thread's wait ran out
-    if (w.full) phases ^= 1u << b;
+    if (Tr::PF && w.full) phases ^= 1u << b;
     QS_TICK(2);
     const long long tph = a.profile ? prof_clock() : 0;  // start of the placement phase
 
@@ -704,8 +725,8 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     const int64_t vend = base + T < end ? base + T : end;
     const int nvalid = static_cast<int>(vend - vstart);
     const int vofs = static_cast<int>(vstart - base);  // window slots before the first valid key
-    K *stage_k = sm.kbuf[b];
-    V *stage_v = sm.vbuf[b];
+    K *stage_k = sm.kbuf[Tr::PF ? b : 0];
+    V *stage_v = sm.vbuf[Tr::PF ? b : 0];
     auto stage = [&](int L) {
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
@@ -801,7 +822,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
             }
         }
     } else if (warp < kDWarps - 1) {
-        if (a.ordered && nx.kind == 1 && nx.full && !nx.a_pub) {
+        if (Tr::PF && a.ordered && nx.kind == 1 && nx.full && !nx.a_pub) {
             // The middle warps first count the prefetched next tile and
             // publish its aggregate, so tiles after it never wait for this CTA
             // to finish the current tile.
@@ -809,7 +830,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
             const bool landed = mbar_wait_bounded(&sm.bar[b ^ 1], (phases >> (b ^ 1)) & 1u, a.ctrl, a.wait_limit_ns);
             if (a.profile && tid == 32) sm.tm[9] += prof_clock() - tmb;
             if (landed) {
-                int cnt = count_low_any<Tr>(sm.kbuf[b ^ 1], nx.pivot, nx.mode);
+                int cnt = count_low_any<Tr>(sm.kbuf[(b ^ 1) % Tr::NBUF], nx.pivot, nx.mode);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
                 if (lane == 0) atomicAdd(&sm.next_low, cnt);
@@ -1066,7 +1087,7 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
     __syncthreads();
     if (a.profile && tid == 0) sm.tm[0] += prof_clock() - t_wait;
     int b = 0;
-    if (sm.w[0].kind == 1 && sm.w[0].full) pending |= 1u;
+    if (Tr::PF && sm.w[0].kind == 1 && sm.w[0].full) pending |= 1u;
     bool aborted = false;
     // The current work item lives in sm.w[0], the next one in sm.w[1].
     while (sm.w[0].kind == 1) {
@@ -1095,7 +1116,7 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
         }
         const int r = partition_tile<Tr>(a, sm.w[0], sm.w[1], sm, b, phases);
         if (r != -1) pending &= ~(1u << b);  // -1: the copy into buffer b was never seen to land
-        if (sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);  // written before the tile's barriers
+        if (Tr::PF && sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);  // written before the tile's barriers
         if (r < 0) {
             aborted = true;
             break;
@@ -1116,7 +1137,7 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
                 if (sm.w[1].kind == 1) issue_tile_load<Tr>(a, sm.w[1], sm, b ^ 1);
             }
             __syncthreads();
-            if (sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);
+            if (Tr::PF && sm.w[1].kind == 1 && sm.w[1].full) pending |= 1u << (b ^ 1);
             if (a.profile && tid == 0) sm.tm[0] += prof_clock() - t0w;
         }
         __syncthreads();

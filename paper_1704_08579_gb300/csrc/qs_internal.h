@@ -159,6 +159,7 @@ struct KernelLimits {
     int64_t leaf_max, small_max, tile;  // tile: the smaller of the two partition tile variants
     size_t driver_smem, leaf_smem;
     int items_wide, items_narrow;       // keys per thread of the two partition tile variants
+    int items_xwide;                    // keys per thread of the register-tile variant (0: none)
     int items_default;                  // the variant used when QS_OPT_DRIVER_ITEMS is 0
 };
 
@@ -183,8 +184,8 @@ uint64_t option_wait_limit_ns();
 KernelLimits limits_i32();
 KernelLimits limits_f64();
 KernelLimits limits_kv();
-// Resident CTAs per SM of the persistent kernel (which = 0) or the leaf
-// kernel (which = 1) of each kind.
+// Resident CTAs per SM of the persistent kernel (which = 0 wide tile, 2
+// narrow tile, 3 register tile) or the leaf kernel (which = 1) of each kind.
 int occupancy_i32(int which, int *blocks_per_sm);
 int occupancy_f64(int which, int *blocks_per_sm);
 int occupancy_kv(int which, int *blocks_per_sm);

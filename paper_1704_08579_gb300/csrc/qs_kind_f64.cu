@@ -8,14 +8,18 @@ namespace {
 // the narrow one is chosen per call by QS_OPT_DRIVER_ITEMS (the autotuner).
 using Tr = Traits<double, false, 8, 16384, 512>;
 using TrN = Traits<double, false, 4, 16384, 512>;
+// Register tile: 32 keys per thread (64 KB), loaded straight into registers, 2 CTAs per SM.
+using TrX = Traits<double, false, 16, 16384, 512, false>;
 // Minimum CTAs per SM of the persistent partition kernel: 3 (80 registers
 // per thread).  The leaf kernel runs one 1024-thread CTA per SM.
 using L = Launcher<Tr, 3 * 256 / kDThreads>;
 using LN = Launcher<TrN, 3 * 256 / kDThreads>;
+using LX = Launcher<TrX, 2>;
 }  // namespace
 
 int launch_f64(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg)
 {
+    if (cfg.items == TrX::E) return LX::launch(a, cfg);
     return cfg.items == TrN::E ? LN::launch(a, cfg) : L::launch(a, cfg);
 }
 KernelLimits limits_f64()
@@ -24,10 +28,14 @@ KernelLimits limits_f64()
     l.tile = TrN::T < Tr::T ? TrN::T : Tr::T;
     l.items_wide = Tr::E;
     l.items_narrow = TrN::E;
+    l.items_xwide = TrX::E;
     l.items_default = Tr::E;
     return l;
 }
-int occupancy_f64(int which, int *bps) { return which == 2 ? LN::occ(0, bps) : L::occ(which, bps); }
+int occupancy_f64(int which, int *bps)
+{
+    return which == 3 ? LX::occ(0, bps) : which == 2 ? LN::occ(0, bps) : L::occ(which, bps);
+}
 int learned_f64(const Args<Tr::K, Tr::V> &a, const LearnedCall &lc, LaunchCfg &cfg) { return L::learned(a, lc, cfg); }
 
 }  // namespace qs

@@ -29,10 +29,11 @@ KernelLimits limits_i32()
     l.tile = TrN::T < Tr::T ? TrN::T : Tr::T;
     l.items_wide = Tr::E;
     l.items_narrow = TrN::E;
+    l.items_xwide = 0;  // a register tile would need 64 keys per thread
     l.items_default = TrN::E;
     return l;
 }
-int occupancy_i32(int which, int *bps) { return which == 2 ? LN::occ(0, bps) : L::occ(which, bps); }
+int occupancy_i32(int which, int *bps) { return which == 2 ? LN::occ(0, bps) : L::occ(which == 3 ? 0 : which, bps); }
 int learned_i32(const Args<Tr::K, Tr::V> &a, const LearnedCall &lc, LaunchCfg &cfg) { return L::learned(a, lc, cfg); }
 
 }  // namespace qs

@@ -8,14 +8,18 @@ namespace {
 // the narrow one is chosen per call by QS_OPT_DRIVER_ITEMS (the autotuner).
 using Tr = Traits<int32_t, true, 4, 16384, 512>;
 using TrN = Traits<int32_t, true, 2, 16384, 512>;
+// Register tile: 32 keys and values per thread (64 KB), loaded straight into registers, 2 CTAs per SM.
+using TrX = Traits<int32_t, true, 8, 16384, 512, false>;
 // Minimum CTAs per SM of the persistent partition kernel: 3 (80 registers
 // per thread).  The leaf kernel runs one 1024-thread CTA per SM.
 using L = Launcher<Tr, 3 * 256 / kDThreads>;
 using LN = Launcher<TrN, 3 * 256 / kDThreads>;
+using LX = Launcher<TrX, 2>;
 }  // namespace
 
 int launch_kv(const Args<Tr::K, Tr::V> &a, LaunchCfg &cfg)
 {
+    if (cfg.items == TrX::E) return LX::launch(a, cfg);
     return cfg.items == TrN::E ? LN::launch(a, cfg) : L::launch(a, cfg);
 }
 KernelLimits limits_kv()
@@ -24,9 +28,13 @@ KernelLimits limits_kv()
     l.tile = TrN::T < Tr::T ? TrN::T : Tr::T;
     l.items_wide = Tr::E;
     l.items_narrow = TrN::E;
+    l.items_xwide = TrX::E;
     l.items_default = Tr::E;
     return l;
 }
-int occupancy_kv(int which, int *bps) { return which == 2 ? LN::occ(0, bps) : L::occ(which, bps); }
+int occupancy_kv(int which, int *bps)
+{
+    return which == 3 ? LX::occ(0, bps) : which == 2 ? LN::occ(0, bps) : L::occ(which, bps);
+}
 
 }  // namespace qs

@@ -197,12 +197,13 @@ def test_capacity_overflow_reported_and_recovers():
     assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
 
 
-@pytest.mark.parametrize("kind,items", [("i32", 32), ("f64", 8), ("kv", 8)])
+@pytest.mark.parametrize("kind,items", [("i32", 32), ("f64", 8), ("kv", 8), ("f64", 32), ("kv", 32)])
 def test_narrow_tile_variant(kind, items):
-    """The partition tile variant that is not the kind's default
+    """The partition tile variants that are not the kind's default
     (QS_OPT_DRIVER_ITEMS: the wide one for int32, the narrow one for FP64
-    and key/value) gives the same results: sorts of several sizes and
-    distributions, and a partition."""
+    and key/value, and the register tile of 32 keys per thread loaded
+    without a prefetch buffer) give the same results: sorts of several sizes
+    and distributions, and a partition."""
     import torch
 
     import oracle
