@@ -197,8 +197,13 @@ int qs_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, in
 /*
  * Host-buffer sorts: h_keys (and h_vals) are HOST pointers (pinned memory is
  * fastest).  The library copies them into a device staging area owned by the
- * workspace, sorts there with the qs_sort_* path, and copies the result back,
- * all on `stream`.  Same return convention as qs_sort_*.
+ * workspace and sorts there with the qs_sort_* path, all on `stream`.  If the
+ * buffers are pinned memory mapped into the device's address space (what
+ * cudaHostAlloc / cudaMallocHost give under unified addressing), the leaf
+ * kernel writes each sorted part straight into them, so the return transfer
+ * overlaps the leaf sorts; otherwise the result is copied back afterwards.
+ * Synchronous: returns once the host buffers hold the result, QS_OK or a
+ * negative qs_status.
  */
 int qs_sort_host_i32(int32_t *h_keys, int64_t n, qs_stream_t stream);
 int qs_sort_host_f64(double *h_keys, int64_t n, qs_stream_t stream);

@@ -330,6 +330,9 @@ Args<K, int32_t> make_args(Workspace &w, int kind, K *keys, int32_t *vals, int64
     a.wait_limit_ns = static_cast<uint64_t>(g_wait_limit_ns.load());
     a.ordered = g_ordered.load();
     a.profile = g_profile.load() >= 2 ? 1 : 0;
+    a.okeys = a.keys[0];
+    a.ovals = a.vals[0];
+    a.out_separate = 0;
     return a;
 }
 
@@ -430,7 +433,8 @@ int check_earlier(Workspace &w, cudaStream_t s)
 // by the next call).
 template <class K>
 int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, int partition_only,
-            qs_stream_t stream, const int64_t *seg_off = nullptr, int64_t nseg = 0, bool force_sync = false)
+            qs_stream_t stream, const int64_t *seg_off = nullptr, int64_t nseg = 0, bool force_sync = false,
+            K *out_keys = nullptr, int32_t *out_vals = nullptr)
 {
     t_error.clear();
     std::memset(&t_stats, 0, sizeof(t_stats));
@@ -462,6 +466,11 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     if ((e = order_after_previous(w, s)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
     if ((e = clear_dirty(w, s)) != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     Args<K, int32_t> a = make_args<K>(w, kind, keys, vals, n);
+    if (out_keys) {  // the sorted result goes to a separate (mapped host) array
+        a.okeys = out_keys;
+        a.ovals = out_vals;
+        a.out_separate = 1;
+    }
     a.pivot_bits = pivot_bits;
     a.partition_only = partition_only;
     if (partition_only) a.ordered = 1;
@@ -563,6 +572,26 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     return partition_only ? static_cast<int64_t>(lt) : QS_OK;
 }
 
+// Device address of a host buffer the GPU can write (pinned memory mapped
+// into the device's address space), or nullptr (pageable memory).
+template <class T>
+T *mapped_device_ptr(T *h)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    if (reinterpret_cast<uintptr_t>(at.devicePointer) % sizeof(T)) return nullptr;
+    return static_cast<T *>(at.devicePointer);
+}
+
+// Host-buffer sort: the keys (and values) are copied into a device staging
+// area and sorted there.  When the host buffers are mapped pinned memory, the
+// leaf kernel writes every sorted part straight into them, so the copy back
+// overlaps the leaf sorts instead of following them; otherwise the result is
+// copied back after the sort.
 template <class K>
 int run_host(int kind, K *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream)
 {
@@ -593,13 +622,20 @@ int run_host(int kind, K *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream
     if (kind == QS_KIND_KV &&
         (e = cudaMemcpyAsync(dv, h_vals, static_cast<size_t>(n) * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "cudaMemcpyAsync(H2D)");
-    const int64_t rc = run<K>(kind, dk, kind == QS_KIND_KV ? dv : nullptr, n, 0, 0, stream, nullptr, 0, true);
+    K *mk = mapped_device_ptr(h_keys);
+    int32_t *mv = kind == QS_KIND_KV ? mapped_device_ptr(h_vals) : nullptr;
+    const bool direct = mk && (kind != QS_KIND_KV || mv);
+    const int64_t rc = run<K>(kind, dk, kind == QS_KIND_KV ? dv : nullptr, n, 0, 0, stream, nullptr, 0, true,
+                              direct ? mk : nullptr, direct ? mv : nullptr);
     if (rc) return static_cast<int>(rc);
-    if ((e = cudaMemcpyAsync(h_keys, dk, static_cast<size_t>(n) * sizeof(K), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(e, "cudaMemcpyAsync(D2H)");
-    if (kind == QS_KIND_KV &&
-        (e = cudaMemcpyAsync(h_vals, dv, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    if (!direct) {
+        if ((e = cudaMemcpyAsync(h_keys, dk, static_cast<size_t>(n) * sizeof(K), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+        if (kind == QS_KIND_KV &&
+            (e = cudaMemcpyAsync(h_vals, dv, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    }
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return QS_OK;
 }

@@ -1005,8 +1005,9 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
         if (sm.nt_ok[i]) publish_task(a.owner, sm.nt[i], -1, kDThreads);
     if (a.profile && tid == 0) sm.tm[28] += prof_clock() - tf;
     for (int i = 0; i < 2; ++i) {
-        // Finished run of equal keys: copy back only if it sits in scratch.
-        if (sm.c_kind[i] != 1 || dst != 1) continue;
+        // Finished run of equal keys: copy back if it sits in scratch, or
+        // wherever it sits when the result goes to a separate array.
+        if (sm.c_kind[i] != 1 || (dst != 1 && !a.out_separate)) continue;
         const int64_t coff = sm.c_off[i], clen = sm.c_len[i];
         const bool small = clen <= a.small_max;
         const int64_t chunks = small ? 1 : (clen + kCopyChunk - 1) / kCopyChunk;
@@ -1023,7 +1024,7 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
                 l.off = coff + q * kCopyChunk;
                 const int64_t rem = clen - q * kCopyChunk;
                 l.len = static_cast<int32_t>(small ? clen : (rem < kCopyChunk ? rem : kCopyChunk));
-                l.flags = kLeafFinal | kLeafScratch;
+                l.flags = kLeafFinal | (dst == 1 ? kLeafScratch : 0);
                 a.leaves[small ? first : first + q] = l;
             }
         }

@@ -108,6 +108,13 @@ struct Args {
     const int64_t *seg_off;  // segmented sort: nseg + 1 offsets into keys (nullptr otherwise)
     int64_t nseg;
     int seg_src;  // buffer holding the segments: 0 caller, 1 scratch
+    // Where the leaf kernel writes the sorted result: keys[0] / vals[0], or a
+    // separate array (a mapped pinned host buffer of the host-buffer sort),
+    // in which case every finished range is copied there, also those that
+    // are finished in place in keys[0].
+    K *okeys;
+    V *ovals;
+    int out_separate;
 };
 
 // Launch description computed by the host and consumed by the per-kind launchers.

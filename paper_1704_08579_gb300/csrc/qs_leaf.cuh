@@ -126,8 +126,8 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
         t0 = t;
     }
     group_sync(bar, nthreads);
-    typename Tr::K *ok = a.keys[0] + l.off;
-    typename Tr::V *ov = a.vals[0] + l.off;
+    typename Tr::K *ok = a.okeys + l.off;
+    typename Tr::V *ov = a.ovals + l.off;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int i = g + r * nthreads;
@@ -153,8 +153,8 @@ __device__ void warp_leaf(const Args<typename Tr::K, typename Tr::V> &a, const L
         k[r] = i < len ? LK::load(gk, gv, i) : LK::largest();
     }
     warp_bitonic_sort<E, S>(k);
-    typename Tr::K *ok = a.keys[0] + l.off;
-    typename Tr::V *ov = a.vals[0] + l.off;
+    typename Tr::K *ok = a.okeys + l.off;
+    typename Tr::V *ov = a.ovals + l.off;
 #pragma unroll
     for (int r = 0; r < E; ++r) {
         const int i = lane * E + r;
@@ -240,11 +240,12 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
         if (gi >= 0) {
             const Leaf l = sm.grp[gi].leaf;
             if (l.flags & kLeafFinal) {
-                const K *gk = a.keys[1] + l.off;
-                const V *gv = a.vals[1] + l.off;
+                const int src = (l.flags & kLeafScratch) ? 1 : 0;
+                const K *gk = a.keys[src] + l.off;
+                const V *gv = a.vals[src] + l.off;
                 for (int i = tid; i < l.len; i += kLThreads) {
-                    a.keys[0][l.off + i] = gk[i];
-                    if constexpr (Tr::KV) a.vals[0][l.off + i] = gv[i];
+                    a.okeys[l.off + i] = gk[i];
+                    if constexpr (Tr::KV) a.ovals[l.off + i] = gv[i];
                 }
             } else {
                 group_leaf<Tr>(a, l, keys, sm.grp[gi].start, sm.grp[gi].nthreads, sm.grp[gi].bar);
@@ -276,9 +277,10 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
             l.flags = __shfl_sync(0xffffffffu, mine.flags, q);
             if (!leaf_ok<Tr>(a, l, true)) continue;
             if (l.flags & kLeafFinal) {
+                const int src = (l.flags & kLeafScratch) ? 1 : 0;
                 for (int i = lane; i < l.len; i += 32) {
-                    a.keys[0][l.off + i] = a.keys[1][l.off + i];
-                    if constexpr (Tr::KV) a.vals[0][l.off + i] = a.vals[1][l.off + i];
+                    a.okeys[l.off + i] = a.keys[src][l.off + i];
+                    if constexpr (Tr::KV) a.ovals[l.off + i] = a.vals[src][l.off + i];
                 }
                 continue;
             }

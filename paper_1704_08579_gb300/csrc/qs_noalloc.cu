@@ -116,6 +116,8 @@ extern "C" int64_t qs_partition_i32_noalloc(int32_t *d_keys, int64_t n, int32_t 
     a.partition_only = 1;
     a.ordered = 1;
     a.profile = 0;
+    a.okeys = a.keys[0];
+    a.ovals = a.vals[0];
     LaunchCfg cfg;
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.stream = s;

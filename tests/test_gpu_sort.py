@@ -169,6 +169,33 @@ def test_sort_host_buffers():
     assert_kv_sorted_equal(k, v, hk, hv, ok, ov)
 
 
+def _pinned(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+@pytest.mark.parametrize("n", [2, 5000, 200_001, (1 << 20) + 3])
+def test_sort_host_pinned_buffers(n):
+    """Pinned (mapped) host buffers: the leaf kernel writes the sorted parts
+    straight into them, and finished runs of equal keys are copied out from
+    whichever buffer they were finished in.  Uniform, 16-distinct and
+    all-equal FP64 keys, int32 keys with 7 distinct values, key/value pairs
+    with 1000 distinct keys, against the oracle."""
+    qs = qs_gpu()
+    cases = [synth.uniform_f64(n, 30), synth.f64_config("few", n, 31), np.full(n, 2.5),
+             synth.mod_i32(n, 32, 7)]
+    for x in cases:
+        h = _pinned(x)
+        qs.sort_host(h)
+        assert_keys_equal(h, oracle_sort(x))
+    k, v = synth.kv_config("mod1000", n, 33)
+    hk, hv = _pinned(k), _pinned(v)
+    qs.sort_host(hk, hv)
+    ok, ov = oracle_sort(k, v)
+    assert_kv_sorted_equal(k, v, hk, hv, ok, ov)
+
+
 def test_wait_limit_reports_timeout_and_recovers():
     """A device-side wait that runs out ends the kernel with QS_ERR_TIMEOUT
     (no hang, no fault); the next call works."""
