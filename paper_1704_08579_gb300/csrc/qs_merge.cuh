@@ -80,7 +80,15 @@ __device__ void group_merge_sort(S (&k)[E], S *sm, int g, int ng, int bar)
         for (int r = 0; r < E; ++r) sm[swz<E>(base + step * r)] = k[r];
     }
     for (int W = 4 * E; W < P; W <<= 1) {
-        group_sync(bar, ng);
+        // A merge level reads and writes only its pair's slots [pa, pa + 2W),
+        // which the previous level's threads of the same pair wrote: while a
+        // pair spans at most 32 runs, those threads are one warp (pairs are
+        // aligned to their width), and the warp alone synchronises.
+        const bool in_warp = 2 * W <= 32 * E;
+        if (in_warp)
+            __syncwarp();
+        else
+            group_sync(bar, ng);
         const int o0 = g * E;
         const int pa = o0 & ~(2 * W - 1);
         const int na = P - pa < W ? P - pa : W;
@@ -121,7 +129,10 @@ __device__ void group_merge_sort(S (&k)[E], S *sm, int g, int ng, int bar)
         const bool rev = (pa & (2 * W)) != 0;  // pa is a multiple of 2W: the output run's parity
         const int base = rev ? pa + na + nb - 1 - d : o0;
         const int step = rev ? -1 : 1;
-        group_sync(bar, ng);
+        if (in_warp)
+            __syncwarp();
+        else
+            group_sync(bar, ng);
 #pragma unroll
         for (int r = 0; r < E; ++r) sm[swz<E>(base + step * r)] = k[r];
     }
