@@ -234,6 +234,24 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
         __syncthreads();
         const int ng = sm.ngroups;
         if (ng == 0) break;
+        if (sm.has_carry) {
+            // The part carried over is the next pass's: pull its keys (and
+            // values) towards L2 now, so that its loads meet L2 instead of HBM
+            // once this pass's sorts are done (one CTA per SM: nothing else
+            // hides that latency).
+            const Leaf nl = sm.carry;
+            const int src = (nl.flags & kLeafScratch) ? 1 : 0;
+            const char *kb = reinterpret_cast<const char *>(a.keys[src] + nl.off);
+            const int64_t kbytes = static_cast<int64_t>(nl.len) * sizeof(K);
+            for (int64_t o = static_cast<int64_t>(tid) * 128; o < kbytes; o += static_cast<int64_t>(kLThreads) * 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(kb + o));
+            if constexpr (Tr::KV) {
+                const char *vb = reinterpret_cast<const char *>(a.vals[src] + nl.off);
+                const int64_t vbytes = static_cast<int64_t>(nl.len) * sizeof(V);
+                for (int64_t o = static_cast<int64_t>(tid) * 128; o < vbytes; o += static_cast<int64_t>(kLThreads) * 128)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(vb + o));
+            }
+        }
         int gi = -1;
         for (int i = 0; i < ng; ++i)
             if (tid >= sm.grp[i].start && tid < sm.grp[i].start + sm.grp[i].nthreads) gi = i;
