@@ -338,8 +338,10 @@ int qs_get_stats(qs_stats *out);
  *                        tile of 32 keys per thread (64 KB, loaded straight
  *                        into registers, no prefetch buffer, 2 CTAs per SM);
  *                        the narrow or register-tile value selects that
- *                        variant, 0 the kind's default (i32 narrow, f64 and
- *                        kv wide), any other value the wide one.
+ *                        variant, any other non-zero value the wide one, 0
+ *                        the kind's default: for sorts i32 wide, f64 and kv
+ *                        the register tile; for partitions i32 narrow, f64
+ *                        and kv wide.
  *   QS_OPT_ORDERED       0 (default): inside a sort, each partition tile
  *                        claims its lower- and upper-side output ranges with
  *                        one atomic add each on its task's two counters, so

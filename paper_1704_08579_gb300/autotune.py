@@ -20,7 +20,7 @@ CACHE_DIR = os.path.join(HERE, "tuning")
 
 LEAF_CHOICES = {"i32": (8192, 16384, 32768), "f64": (4096, 8192, 16384), "kv": (4096, 8192, 16384)}
 SMALL_CHOICES = (128, 256, 512)
-ITEMS_CHOICES = {"i32": (16, 32), "f64": (16, 8, 32), "kv": (16, 8, 32)}  # the kind's default first
+ITEMS_CHOICES = {"i32": (32, 16), "f64": (32, 16, 8), "kv": (32, 16, 8)}  # the kind's sort default first
 
 
 def _cache_path(gpu_name: str) -> str:

@@ -482,7 +482,7 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     cfg.stream = s;
     const int64_t ctas = g_driver_ctas.load();
     cfg.items = static_cast<int>(g_driver_items.load());
-    if (cfg.items == 0) cfg.items = limits_of(kind).items_default;
+    if (cfg.items == 0) cfg.items = partition_only ? limits_of(kind).items_default_part : limits_of(kind).items_default;
     cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][tile_variant(kind, cfg.items)];
     cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];
     cfg.profile = g_profile.load();

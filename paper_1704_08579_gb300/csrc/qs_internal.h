@@ -167,7 +167,8 @@ struct KernelLimits {
     size_t driver_smem, leaf_smem;
     int items_wide, items_narrow;       // keys per thread of the two partition tile variants
     int items_xwide;                    // keys per thread of the register-tile variant (0: none)
-    int items_default;                  // the variant used when QS_OPT_DRIVER_ITEMS is 0
+    int items_default;                  // the variant a sort uses when QS_OPT_DRIVER_ITEMS is 0
+    int items_default_part;             // the variant a partition-only call uses then
 };
 
 // Per-kind entry points implemented in qs_kind_{i32,f64,kv}.cu.  They enqueue

@@ -4,8 +4,11 @@
 namespace qs {
 
 namespace {
-// Two partition tile variants (items per thread); the wide one is the default,
-// the narrow one is chosen per call by QS_OPT_DRIVER_ITEMS (the autotuner).
+// Three partition tile variants (items per thread), chosen per call by
+// QS_OPT_DRIVER_ITEMS (the autotuner): wide and narrow prefetched tiles, and
+// the register tile.  Sorts default to the register tile (2^28: 12.84 against 12.97 ms of partition passes),
+// partitions to the wide tile (the register tile's partition lacks the
+// early published aggregates of prefetched tiles: 1.72 against 1.01 ms).
 using Tr = Traits<double, false, 8, 16384, 512>;
 using TrN = Traits<double, false, 4, 16384, 512>;
 // Register tile: 32 keys per thread (64 KB), loaded straight into registers, 2 CTAs per SM.
@@ -29,7 +32,8 @@ KernelLimits limits_f64()
     l.items_wide = Tr::E;
     l.items_narrow = TrN::E;
     l.items_xwide = TrX::E;
-    l.items_default = Tr::E;
+    l.items_default = TrX::E;
+    l.items_default_part = Tr::E;
     return l;
 }
 int occupancy_f64(int which, int *bps)

@@ -5,11 +5,9 @@ namespace qs {
 
 namespace {
 // Two partition tile variants (items per thread), chosen per call by
-// QS_OPT_DRIVER_ITEMS (the autotuner).  For int32 the narrow one is the
-// default: at 4 CTAs per SM (64 registers) it sorts 2^28 keys in 12.96 ms
-// against 13.40 ms for the wide one at 3.  (FP64 and key/value sorts are
-// faster with the wide tile: 16.1 vs 17.0 ms and 16.9 vs 17.5 ms of
-// partition passes at 2^28.)
+// QS_OPT_DRIVER_ITEMS (the autotuner).  Sorts default to the wide one (2^28
+// keys: 8.08 ms of partition passes against 8.39 for the narrow one at 4 CTAs
+// per SM); partitions keep the narrow one.
 using Tr = Traits<int32_t, false, 8, 32768, 512>;
 using TrN = Traits<int32_t, false, 4, 32768, 512>;
 // Minimum CTAs per SM of the persistent partition kernel: 3 (80 registers
@@ -30,7 +28,8 @@ KernelLimits limits_i32()
     l.items_wide = Tr::E;
     l.items_narrow = TrN::E;
     l.items_xwide = 0;  // a register tile would need 64 keys per thread
-    l.items_default = TrN::E;
+    l.items_default = Tr::E;
+    l.items_default_part = TrN::E;
     return l;
 }
 int occupancy_i32(int which, int *bps) { return which == 2 ? LN::occ(0, bps) : L::occ(which == 3 ? 0 : which, bps); }

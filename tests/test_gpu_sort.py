@@ -224,13 +224,14 @@ def test_capacity_overflow_reported_and_recovers():
     assert_keys_equal(_sort_dev(qs, x), oracle_sort(x))
 
 
-@pytest.mark.parametrize("kind,items", [("i32", 32), ("f64", 8), ("kv", 8), ("f64", 32), ("kv", 32)])
+@pytest.mark.parametrize("kind,items", [("i32", 16), ("i32", 32), ("f64", 8), ("f64", 16), ("f64", 32), ("kv", 8),
+                                        ("kv", 16), ("kv", 32)])
 def test_narrow_tile_variant(kind, items):
-    """The partition tile variants that are not the kind's default
-    (QS_OPT_DRIVER_ITEMS: the wide one for int32, the narrow one for FP64
-    and key/value, and the register tile of 32 keys per thread loaded
-    without a prefetch buffer) give the same results: sorts of several sizes
-    and distributions, and a partition."""
+    """Every partition tile variant chosen explicitly (QS_OPT_DRIVER_ITEMS:
+    narrow and wide prefetched tiles, and for FP64 and key/value the register
+    tile of 32 keys per thread loaded without a prefetch buffer) gives the
+    same results: sorts of several sizes and distributions, and a partition
+    (which otherwise uses its own default tile)."""
     import torch
 
     import oracle
