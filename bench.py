@@ -373,18 +373,28 @@ def run_ours(args):
 
 def _e2e(torch, qs, host, stream, args):
     """Same metric through qs_sort_host_f64: pinned host buffer in, sorted host buffer out."""
-    steps = max(1, min(args.steps, 4))
-    pinned = [torch.from_numpy(host).pin_memory() for _ in range(steps + 1)]
+    steps = max(3, min(args.steps, 6))
+    pinned = [torch.from_numpy(host).pin_memory() for _ in range(3)]
     arrs = [p.numpy() for p in pinned]
     qs.sort_host(arrs[0], stream=stream)  # warm-up (allocates the staging area)
-    t0 = time.perf_counter()
-    for a in arrs[1:]:
+    times = []
+    for i in range(steps):
+        a = arrs[1 + i % 2]
+        if i >= 2:
+            a[:] = host  # a fresh unsorted copy (not timed)
+        t0 = time.perf_counter()
         qs.sort_host(a, stream=stream)
-    dt = (time.perf_counter() - t0) / steps
+        times.append(time.perf_counter() - t0)
+    dt = statistics.median(times)
     ok = bool(np.all(arrs[1][1:] >= arrs[1][:-1]))
     del pinned, arrs
+    # The host link is shared with other jobs on the machine; the median step
+    # is reported, with the fastest and slowest beside it.
     return {"value": N_KEYS / dt / 1e9, "unit": "Gkeys/s", "h2d_bytes_per_step": N_KEYS * 8,
-            "d2h_bytes_per_step": N_KEYS * 8, "ms_per_step": dt * 1e3, "steps": steps, "sorted": ok}
+            "d2h_bytes_per_step": N_KEYS * 8, "ms_per_step": dt * 1e3, "ms_min": min(times) * 1e3,
+            "ms_max": max(times) * 1e3, "steps": steps, "sorted": ok,
+            "path": "qs_sort_host_f64 on pinned (mapped) host buffers: H2D copy, sort, result written by the "
+                    "leaf kernel straight into the host buffer"}
 
 
 def _batched(torch, qs, stream, nseg=20_000, steps=3):
