@@ -713,6 +713,25 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     if (a.profile && tid == 0) sm.tm[18] += prof_clock() - tprev;  // own work, before the barrier
     if (__syncthreads_or(landed ? 0 : 1)) return -1;  // CTA-uniform: some thread's wait ran out
     if (Tr::PF && w.full) phases ^= 1u << b;
+    if constexpr (!Tr::PF) {
+        // Register tile: the next tile (resolved by thread 0 before this
+        // one, visible since the barrier) is pulled towards L2 now, a whole
+        // placement + write-out phase before its loads are issued.
+        if (nx.kind == 1 && nx.full) {
+            const int64_t nbase = nx.w0 + static_cast<int64_t>(nx.tile) * T;
+            const char *kb = reinterpret_cast<const char *>(a.keys[nx.src] + nbase);
+            constexpr int kLines = T * static_cast<int>(sizeof(K)) / 128;
+#pragma unroll
+            for (int q = tid; q < kLines; q += kDThreads) asm volatile("prefetch.global.L2 [%0];" ::"l"(kb + q * 128));
+            if constexpr (Tr::KV) {
+                const char *vb = reinterpret_cast<const char *>(a.vals[nx.src] + nbase);
+                constexpr int vLines = T * static_cast<int>(sizeof(V)) / 128;
+#pragma unroll
+                for (int q = tid; q < vLines; q += kDThreads)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(vb + q * 128));
+            }
+        }
+    }
     QS_TICK(2);
     const long long tph = a.profile ? prof_clock() : 0;  // start of the placement phase
 
