@@ -342,7 +342,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "n": N_KEYS, "distribution": "uniform", "parallelism":
                    "replicas" if world > 1 else "single-gpu",
                    "l2": "inputs larger than L2: every step sorts its own 2 GiB pristine copy"},
-        "roofline": {"bound": "hbm", "kernel": "driver_kernel (persistent partition passes)",
+        "roofline": {"bound": "hbm", "kernel": "driver_kernel (persistent partition passes, register tile)",
                      "achieved": achieved, "peak": hbm_peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel_ms": drv_ms,
