@@ -227,6 +227,22 @@ __device__ __forceinline__ void load_splitters(typename KeyOps<typename Tr::K>::
 template <class K>
 constexpr int bucket_e() { return sizeof(K) == 8 ? 8 : 16; }
 
+// Pulls the lines of the chunk's tiles after the current one towards L2 (the
+// bucket kernels process their chunk tile by tile; each tile's loads would
+// otherwise wait on HBM with nothing else in flight).  One 128-byte line per
+// thread and tile, `ahead` tiles of `tile` elements starting at `from`.
+template <class T>
+__device__ __forceinline__ void prefetch_tiles_l2(const T *p, int64_t from, int64_t hi, int tile, int ahead)
+{
+    constexpr int kPerLine = 128 / static_cast<int>(sizeof(T));
+    for (int t = 0; t < ahead; ++t) {
+        const int64_t first = from + static_cast<int64_t>(t) * tile;
+        for (int64_t e = first + static_cast<int64_t>(threadIdx.x) * kPerLine; e < first + tile && e < hi;
+             e += static_cast<int64_t>(kThreads) * kPerLine)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(p + e));
+    }
+}
+
 template <class Tr>
 __global__ void __launch_bounds__(kThreads) bucket_hist_kernel(const typename Tr::K *__restrict__ keys, int64_t n,
                                                                LearnedBufs<typename Tr::K> lb, int nsplit)
@@ -241,6 +257,11 @@ __global__ void __launch_bounds__(kThreads) bucket_hist_kernel(const typename Tr
     const int64_t c = blockIdx.x, g = gridDim.x;
     const int64_t lo = c * n / g, hi = (c + 1) * n / g;
     for (int64_t base = lo; base < hi; base += TILE) {
+        // Keep two tiles ahead in L2 (the first tile also covers itself).
+        if (base == lo)
+            prefetch_tiles_l2(keys, base, hi, TILE, 3);
+        else
+            prefetch_tiles_l2(keys, base + 2 * TILE, hi, TILE, 1);
         // E independent loads and searches per thread, then one shared-memory
         // add per key into the warp's own histogram.
         typename Ops::S k[E];
@@ -404,6 +425,11 @@ __global__ void __launch_bounds__(kThreads) bucket_scatter_kernel(Args<typename 
     K *__restrict__ dk = a.keys[1];
     V *__restrict__ dv = a.vals[1];
     for (int64_t base = lo; base < hi; base += TILE) {
+        // Keep two tiles ahead in L2 (the first tile also covers itself).
+        const int64_t pf = base == lo ? base : base + 2 * TILE;
+        const int pn = base == lo ? 3 : 1;
+        prefetch_tiles_l2(sk, pf, hi, TILE, pn);
+        if constexpr (Tr::KV) prefetch_tiles_l2(sv, pf, hi, TILE, pn);
         const int cnt = static_cast<int>(hi - base < TILE ? hi - base : TILE);
         K key[E];
         V val[Tr::KV ? E : 1];
