@@ -301,13 +301,19 @@ typedef struct {
      * group [20] loading, [21] the network, [23] storing, and [22] padding
      * slots sorted; [24] resolving the next ticket, [25] issuing its load
      * (thread 0); [26] sampling the children's pivots, [27] allocating them,
-     * [28] publishing their tickets (task completion). */
-    int64_t driver_cycles[32];
+     * [28] publishing their tickets (task completion); leaf kernel's
+     * mid-range splits (thread 0): [29] cycles in splits, [30] splits,
+     * [31] pivot sampling, [32] loading and counting the chunks, [33]
+     * waiting at the chunk barrier, [34] scan and placement. */
+    int64_t driver_cycles[40];
     int64_t bucket_max;     /* learned / bucket pass: largest bucket */
     int64_t bucket_over;    /* learned / bucket pass: buckets above 4x their even share */
     int64_t bucket_dev;     /* learned / bucket pass: sum over the B buckets of |size * B - n|;
                                bucket_dev / (2 n B) is the imbalance error (total variation
                                distance between the bucket sizes and an even split) */
+    int64_t mid_parts;      /* parts the leaf kernel split once itself (larger than one CTA's
+                               shared memory holds: 16384 keys for f64 / kv, 32768 for i32) */
+    int64_t mid_keys;       /* their keys: each read once more and written once more, in L2 */
 } qs_stats;
 
 int qs_get_stats(qs_stats *out);
@@ -327,9 +333,14 @@ int qs_get_stats(qs_stats *out);
  *   QS_OPT_DRIVER_CTAS   if > 0, number of CTAs of the persistent kernels;
  *                        0 = all resident CTAs.
  *   QS_OPT_LEAF_MAX      parts of at most this many keys (a power of two,
- *                        >= 32) go to the Bitonic leaf kernel; 0 = the
- *                        compiled maximum (16384 f64/kv, 32768 i32), larger
- *                        values are clamped to it.
+ *                        >= 32) go to the leaf kernel; 0 = what one CTA's
+ *                        shared memory sorts (16384 f64/kv, 32768 i32).
+ *                        Up to twice that is accepted (larger values are
+ *                        clamped): a part above the shared-memory size is
+ *                        then split once around a sampled pivot by the leaf
+ *                        kernel's CTA itself, through L2, instead of by one
+ *                        more device-wide partition pass (measured slower on
+ *                        GB300 for uniform keys, hence not the default).
  *   QS_OPT_SMALL_MAX     parts of at most this many keys (power of two, >= 32)
  *                        are sorted by one warp; 0 = the compiled maximum 512.
  *   QS_OPT_DRIVER_ITEMS  keys per thread of a partition tile: each kind has a

@@ -54,8 +54,8 @@ class Stats(ctypes.Structure):
         "n", "kind", "part_tasks", "part_keys", "leaf_parts", "leaf_keys", "copy_keys", "max_depth",
         "lookback_words", "grid_driver", "grid_leaf")] + [
         (name, ctypes.c_double) for name in ("ms_driver", "ms_leaf", "ms_copy", "ms_total")] + [
-        ("driver_cycles", ctypes.c_int64 * 32), ("bucket_max", ctypes.c_int64), ("bucket_over", ctypes.c_int64),
-        ("bucket_dev", ctypes.c_int64)]
+        ("driver_cycles", ctypes.c_int64 * 40), ("bucket_max", ctypes.c_int64), ("bucket_over", ctypes.c_int64),
+        ("bucket_dev", ctypes.c_int64), ("mid_parts", ctypes.c_int64), ("mid_keys", ctypes.c_int64)]
 
 
 def header_functions() -> list[str]:

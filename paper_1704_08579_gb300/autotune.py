@@ -1,5 +1,5 @@
 """Autotuner for the run-time knobs of the sort: the leaf threshold (largest
-part handed to the Bitonic kernel, QS_OPT_LEAF_MAX), the one-warp threshold
+part handed to the leaf kernel, QS_OPT_LEAF_MAX), the one-warp threshold
 (QS_OPT_SMALL_MAX) and the keys per thread of a partition tile
 (QS_OPT_DRIVER_ITEMS, one of the compiled tile variants).  Each candidate
 is timed on the caller's own data with CUDA events (a fresh copy of the input
@@ -18,7 +18,9 @@ import paper_1704_08579_gb300 as qs
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_DIR = os.path.join(HERE, "tuning")
 
-LEAF_CHOICES = {"i32": (8192, 16384, 32768), "f64": (4096, 8192, 16384), "kv": (4096, 8192, 16384)}
+# The last choice of each kind hands parts of up to twice the shared-memory
+# size to the leaf kernel, which then splits them once itself.
+LEAF_CHOICES = {"i32": (8192, 16384, 32768, 65536), "f64": (4096, 8192, 16384, 32768), "kv": (4096, 8192, 16384, 32768)}
 SMALL_CHOICES = (128, 256, 512)
 ITEMS_CHOICES = {"i32": (32, 16), "f64": (32, 16, 8), "kv": (32, 16, 8)}  # the kind's sort default first
 

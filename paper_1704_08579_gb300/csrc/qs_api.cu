@@ -26,7 +26,7 @@ std::atomic<int> g_profile{0};  // 1: CUDA events around kernels; 2: also in-ker
 std::atomic<int64_t> g_wait_limit_ns{2000000000ll};
 std::atomic<int64_t> g_task_cap{0};
 std::atomic<int64_t> g_driver_ctas{0};
-std::atomic<int64_t> g_leaf_max{0};   // 0 = the kind's compiled maximum
+std::atomic<int64_t> g_leaf_max{0};   // 0 = the kind's default (one CTA's shared memory)
 std::atomic<int64_t> g_small_max{0};  // 0 = the kind's compiled maximum
 std::atomic<int64_t> g_driver_items{0};  // 0 = the kind's default partition tile
 std::atomic<int> g_ordered{0};  // 1 = the sort's partitions place tiles in input order too
@@ -184,8 +184,10 @@ int tile_variant(int kind, int items)
 
 int64_t leaf_max_of(int kind)
 {
-    const int64_t compiled = limits_of(kind).leaf_max, want = g_leaf_max.load();
-    return want > 0 && want < compiled ? want : compiled;
+    const KernelLimits l = limits_of(kind);
+    const int64_t want = g_leaf_max.load();
+    if (want <= 0) return l.leaf_default;
+    return want < l.leaf_max ? want : l.leaf_max;
 }
 
 int64_t small_max_of(int kind)
@@ -379,6 +381,8 @@ void stats_from_ctrl(const Workspace &w)
     t_stats.leaf_keys = static_cast<int64_t>(c.leaf_keys);
     t_stats.copy_keys = static_cast<int64_t>(c.copy_keys);
     t_stats.max_depth = static_cast<int64_t>(c.max_depth);
+    t_stats.mid_parts = static_cast<int64_t>(c.mid_parts);
+    t_stats.mid_keys = static_cast<int64_t>(c.mid_keys);
     t_stats.lookback_words = static_cast<int64_t>(c.pool_cursor);
     t_stats.grid_driver = w.last_grid_driver;
     t_stats.grid_leaf = w.last_grid_leaf;

@@ -40,52 +40,6 @@
 namespace qs {
 
 // ---------------------------------------------------------------------------
-// Pivot selection.  The paper's experiments use a median of three values
-// (Section IV-A); here the median of 64 keys sampled at jittered strides over
-// the range: element 32 of the 64 in sorted order.  It is found by rank, not
-// by sorting: every lane counts, for its two samples, the samples below and
-// not above them, reading all 64 with independent shuffles -- a sort would be
-// a chain of ~20 dependent shuffle stages, each queued behind the other
-// CTAs' shared-memory traffic.  Called by a full warp; returns the pivot's
-// raw bits (int32 sign-extended, or IEEE bits).
-// ---------------------------------------------------------------------------
-template <class K>
-__device__ uint64_t sample_median(const K *src, int64_t off, int64_t len, uint64_t salt)
-{
-    using Ops = KeyOps<K>;
-    using S = typename Ops::S;
-    const int lane = threadIdx.x & 31;
-    S s[2];
-    const int64_t stride = len / 64;  // len > 64 for every partition task
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        const int i = lane * 2 + r;
-        const uint64_t h = mix64(salt * 64 + i);
-        const int64_t jitter = static_cast<int64_t>(h % static_cast<uint64_t>(stride > 0 ? stride : 1));
-        s[r] = Ops::to_s(__ldcg(src + off + (static_cast<int64_t>(i) * len) / 64 + jitter));
-    }
-    int lt[2] = {0, 0}, le[2] = {0, 0};
-#pragma unroll 8
-    for (int j = 0; j < 32; ++j) {
-        const S o0 = __shfl_sync(0xffffffffu, s[0], j);
-        const S o1 = __shfl_sync(0xffffffffu, s[1], j);
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            lt[r] += (o0 < s[r] ? 1 : 0) + (o1 < s[r] ? 1 : 0);
-            le[r] += (o0 <= s[r] ? 1 : 0) + (o1 <= s[r] ? 1 : 0);
-        }
-    }
-    // Element 32 of the sorted samples is a sample x with lt(x) <= 32 < le(x).
-    const bool h0 = lt[0] <= 32 && 32 < le[0];
-    const bool h1 = lt[1] <= 32 && 32 < le[1];
-    const unsigned m0 = __ballot_sync(0xffffffffu, h0);
-    const unsigned m1 = __ballot_sync(0xffffffffu, h1);
-    const int from = m0 ? __ffs(m0) - 1 : __ffs(m1) - 1;
-    const S x = __shfl_sync(0xffffffffu, h0 ? s[0] : s[1], from);
-    return Ops::to_bits(Ops::from_s(x));
-}
-
-// ---------------------------------------------------------------------------
 // Task creation and leaf listing (called by one thread).
 // ---------------------------------------------------------------------------
 struct NewTask {
@@ -1221,6 +1175,7 @@ __global__ void __launch_bounds__(kThreads) setup_kernel(Args<typename Tr::K, ty
         c->status = 0;
         c->info = 0;
         c->part_tasks = c->part_keys = c->leaf_parts = c->leaf_keys = c->copy_keys = c->max_depth = 0;
+        c->mid_parts = c->mid_keys = 0;
         c->lt_result = 0;
         c->exited = 0;
         for (int i = 0; i < kProfSlots; ++i) c->cycles[i] = 0;

@@ -67,7 +67,7 @@ struct alignas(16) Leaf {
 constexpr int kLeafScratch = 1;
 constexpr int kLeafFinal = 2;
 
-constexpr int kProfSlots = 32;  // driver profiling slots (qs_stats.driver_cycles)
+constexpr int kProfSlots = 40;  // driver profiling slots (qs_stats.driver_cycles)
 
 struct alignas(128) Ctrl {
     unsigned long long ticket_head;  // next ticket to hand out
@@ -79,6 +79,7 @@ struct alignas(128) Ctrl {
     int sticky, sticky_info;  // first error of an earlier call not yet reported to the host
     // statistics
     unsigned long long part_tasks, part_keys, leaf_parts, leaf_keys, copy_keys, max_depth;
+    unsigned long long mid_parts, mid_keys;  // parts split once by the leaf kernel, their keys
     unsigned long long lt_result;  // split index of a partition-only call
     unsigned long long exited;     // CTAs of the persistent kernel that left cleanly
     unsigned long long cycles[kProfSlots];  // per-phase SM cycles and counters (profiling on)
@@ -98,7 +99,7 @@ struct Args {
     Leaf *leaves;
     Ctrl *ctrl;
     int64_t task_cap, pool_cap, leaf_cap;  // owner and pool hold pool_cap entries
-    int64_t leaf_max;   // parts up to this size go to the Bitonic kernel
+    int64_t leaf_max;   // parts up to this size go to the leaf kernel
     int64_t small_max;  // parts up to this size are sorted by one warp
     uint64_t wait_limit_ns;
     uint64_t pivot_bits;  // partition-only: the caller's pivot
@@ -164,6 +165,11 @@ struct LearnedCall {
 
 struct KernelLimits {
     int64_t leaf_max, small_max, tile;  // tile: the smaller of the two partition tile variants
+    // leaf_max: the largest part the leaf kernel takes (a part above
+    // leaf_default is split once by the leaf kernel itself); leaf_default:
+    // the threshold used when QS_OPT_LEAF_MAX is 0 (what one CTA's shared
+    // memory sorts)
+    int64_t leaf_default;
     size_t driver_smem, leaf_smem;
     int items_wide, items_narrow;       // keys per thread of the two partition tile variants
     int items_xwide;                    // keys per thread of the register-tile variant (0: none)

@@ -19,7 +19,8 @@ struct Launcher {
     static KernelLimits limits()
     {
         KernelLimits l;
-        l.leaf_max = Tr::LEAF;
+        l.leaf_max = Tr::MID;
+        l.leaf_default = Tr::LEAF;
         l.small_max = Tr::SMALL;
         l.tile = Tr::T;
         l.driver_smem = kDriverSmem;

@@ -6,6 +6,13 @@
 // CTA.  Parts of at most SMALL keys take one warp each and the Bitonic
 // network alone (registers + shuffles).  The tail of a part is padded with
 // the largest sort-space key (Section III-A-3).
+//
+// Mid-range parts (LEAF < len <= MID = 2 * LEAF keys, more than one CTA's
+// shared memory holds) take the whole CTA for one more quicksort step of
+// their own: a sampled pivot, one partition pass from the part's buffer into
+// the other one (Section III-B's two write cursors, as in the device-wide
+// pass), and the two sides are then sorted like listed parts -- while they
+// are still in L2, instead of after one more device-wide pass through HBM.
 #pragma once
 
 #include <type_traits>
@@ -71,6 +78,7 @@ struct LeafGroup {
 // Named barriers 1..15 are available to groups (barrier 0 is __syncthreads).
 constexpr int kLeafBarriers = 15;
 
+
 template <class Tr>
 struct LeafSmem {
     LeafGroup grp[kLThreads / 32];
@@ -78,13 +86,22 @@ struct LeafSmem {
     int has_carry;
     int ngroups;
     long long idx;
+    // Sides of this CTA's last mid-range split still to be sorted (the
+    // sortable side on top).  A split runs alone in its pass and pushes at
+    // most two sides; the packing loop takes pending sides before any other
+    // part and splits the next part only once it is alone in a pass, so the
+    // stack holds at most the two sides of one split (a side that does not
+    // fit is carried, not pushed back).
+    static constexpr int kSides = 8;
+    Leaf side[kSides];
+    int nside;
 };
 
 // A listed part must lie inside the array and fit the kernel that takes it.
 template <class Tr>
 __device__ bool leaf_ok(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l, bool small)
 {
-    const int64_t cap = (l.flags & kLeafFinal) ? (small ? a.small_max : kCopyChunk) : (small ? a.small_max : Tr::LEAF);
+    const int64_t cap = (l.flags & kLeafFinal) ? (small ? a.small_max : kCopyChunk) : (small ? a.small_max : Tr::MID);
     const bool ok = l.off >= 0 && l.len > 0 && l.len <= cap && l.off + l.len <= a.n;
     if (!ok) set_error(a.ctrl, kErrInternalIndex, 3);
     return ok;
@@ -162,6 +179,204 @@ __device__ void warp_leaf(const Args<typename Tr::K, typename Tr::V> &a, const L
     }
 }
 
+// Sort-space image of a key given by its raw bits (int32 sign-extended, or
+// IEEE bits), as sample_median returns it.
+template <class K>
+__device__ __forceinline__ typename KeyOps<K>::S s_of_bits(uint64_t b)
+{
+    if constexpr (sizeof(K) == 8)
+        return KeyOps<K>::to_s(__longlong_as_double(static_cast<long long>(b)));
+    else
+        return KeyOps<K>::to_s(static_cast<K>(static_cast<int64_t>(b)));
+}
+
+// Copies a finished side from the buffer it sits in to the output (the
+// calling group: thread g of ng).
+template <class Tr>
+__device__ void copy_out(const Args<typename Tr::K, typename Tr::V> &a, int64_t off, int len, int buf, int g, int ng)
+{
+    if (buf == 0 && !a.out_separate) return;  // already in place
+    for (int i = g; i < len; i += ng) {
+        a.okeys[off + i] = a.keys[buf][off + i];
+        if constexpr (Tr::KV) a.ovals[off + i] = a.vals[buf][off + i];
+    }
+}
+
+// Per-group state of a mid-range split, kept at the start of the group's own
+// slice of the leaf kernel's shared memory (a split sorts nothing there).
+struct MidState {
+    unsigned tot[2][32];  // per warp: lower-side keys | valid keys << 16 (two chunks in flight)
+    uint64_t pivot;       // the pivot's raw bits
+    int eq;               // pivot-equal keys of the part
+};
+static_assert(sizeof(MidState) <= 64 * 16 * 4, "fits the smallest split group's slice");
+
+// One quicksort step of a mid-range part by a group of ng threads (thread g,
+// named barrier `bar`; the packing loop gives it the whole CTA, alone in its
+// pass).  The pivot is the median of 64 sampled keys.  A chunk of ng*E keys at a
+// time is loaded (thread g takes keys g, g + ng, ...), compared, and ranked
+// with warp ballots: within a warp, the lower-side keys of a round take
+// consecutive slots; across the group's warps, a scan of the per-warp
+// totals.  Keys are written straight to the other buffer: lower side forward
+// from the part's start, upper side backward from its end (the two write
+// cursors of Section III-B); the sides are sorted next, so the order inside
+// them is free.  Equal keys as in the device-wide pass: if nothing is below
+// the pivot the pass is repeated with '<=', whose lower side holds only
+// pivot-equal keys and is finished; a side of only pivot-equal keys is
+// finished too.  Finished sides are copied to the output at once; the others
+// are left on sm.side for the packing loop.
+template <class Tr>
+__device__ __noinline__ void mid_split(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l, LeafSmem<Tr> &sm,
+                                       MidState &ms, int g, int ng, int bar)
+{
+    using K = typename Tr::K;
+    using V = typename Tr::V;
+    using Ops = KeyOps<K>;
+    using S = typename Ops::S;
+    constexpr int E = LeafCfg<Tr>::E;  // keys per thread and chunk
+    const int lane = g & 31, gw = g >> 5, nw = ng >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int src = (l.flags & kLeafScratch) ? 1 : 0, dst = src ^ 1;
+    const int len = l.len;
+    const K *gk = a.keys[src] + l.off;
+    const V *gv = a.vals[src] + l.off;
+    K *dk = a.keys[dst] + l.off;
+    V *dv = a.vals[dst] + l.off;
+    const bool lead = a.profile && g == 0;
+    const long long tq = lead ? prof_clock() : 0;
+    if (gw == 0) {
+        const uint64_t pb =
+            sample_median<K>(a.keys[src], l.off, len, static_cast<uint64_t>(l.off) * 0x9E3779B97F4A7C15ull + len);
+        if (lane == 0) {
+            ms.pivot = pb;
+            ms.eq = 0;
+            atomicAdd(&a.ctrl->mid_parts, 1ull);
+        }
+    }
+    group_sync(bar, ng);
+    if (lead) atomicAdd(&a.ctrl->cycles[31], static_cast<unsigned long long>(prof_clock() - tq));
+    const S ps = s_of_bits<K>(ms.pivot);
+    const int chunk = ng * E;
+    bool le = false;  // '<' first
+    int low = 0, par = 0;
+    for (;;) {
+        if (g == 0) atomicAdd(&a.ctrl->mid_keys, static_cast<unsigned long long>(len));
+        int lo_base = 0, hi_base = 0;
+        for (int c0 = 0; c0 < len; c0 += chunk, par ^= 1) {
+            long long tc = lead ? prof_clock() : 0;
+            const int nv = len - c0 < chunk ? len - c0 : chunk;
+            K k[E];
+            V v[Tr::KV ? E : 1];
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int i = r * ng + g;
+                k[r] = i < nv ? __ldcg(gk + c0 + i) : K(0);
+                if constexpr (Tr::KV) v[r] = i < nv ? __ldcg(gv + c0 + i) : 0;
+            }
+            // This warp's lower-side, valid and pivot-equal keys.
+            int wl = 0, wv = 0, eq = 0;
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const bool ok = r * ng + g < nv;
+                const S s = Ops::to_s(k[r]);
+                wl += __popc(__ballot_sync(0xffffffffu, ok && (le ? s <= ps : s < ps)));
+                eq += ok && s == ps ? 1 : 0;
+                const int rem = nv - (r * ng + gw * 32);  // the valid lanes of a round are a prefix
+                wv += rem <= 0 ? 0 : (rem >= 32 ? 32 : rem);
+            }
+            if (!le) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) eq += __shfl_xor_sync(0xffffffffu, eq, o);
+                if (lane == 0 && eq) atomicAdd(&ms.eq, eq);
+            }
+            // Both counts in one word (each sum stays below 2^16 keys).
+            if (lane == 0) ms.tot[par][gw] = static_cast<unsigned>(wl) | (static_cast<unsigned>(wv) << 16);
+            if (lead) {
+                const long long now = prof_clock();
+                atomicAdd(&a.ctrl->cycles[32], static_cast<unsigned long long>(now - tc));
+                tc = now;
+            }
+            group_sync(bar, ng);
+            if (lead) {
+                const long long now = prof_clock();
+                atomicAdd(&a.ctrl->cycles[33], static_cast<unsigned long long>(now - tc));
+                tc = now;
+            }
+            // Exclusive scan of the per-warp totals (every warp the same).
+            const unsigned t = lane < nw ? ms.tot[par][lane] : 0u;
+            unsigned incl = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned x = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += x;
+            }
+            const unsigned all = __shfl_sync(0xffffffffu, incl, 31);
+            const unsigned before = __shfl_sync(0xffffffffu, incl - t, gw);
+            const int L = static_cast<int>(all & 0xffffu);
+            const int lb = static_cast<int>(before & 0xffffu), vb0 = static_cast<int>(before >> 16);
+            int lpre = lo_base + lb;         // lower-side slots before this warp
+            int hpre = hi_base + (vb0 - lb);  // upper-side slots before it
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const bool ok = r * ng + g < nv;
+                const bool lo = ok && (le ? Ops::to_s(k[r]) <= ps : Ops::to_s(k[r]) < ps);
+                const unsigned b = __ballot_sync(0xffffffffu, lo);
+                const unsigned vb = __ballot_sync(0xffffffffu, ok);
+                const int lr = __popc(b & lt_mask);
+                if (ok) {
+                    const int pos = lo ? lpre + lr : len - 1 - (hpre + __popc(vb & ~b & lt_mask));
+                    dk[pos] = k[r];
+                    if constexpr (Tr::KV) dv[pos] = v[r];
+                }
+                lpre += __popc(b);
+                hpre += __popc(vb & ~b);
+            }
+            lo_base += L;
+            hi_base += nv - L;
+            if (lead) atomicAdd(&a.ctrl->cycles[34], static_cast<unsigned long long>(prof_clock() - tc));
+        }
+        low = lo_base;
+        // Uniform decision: lo_base and ms.eq are the same in every thread.
+        if (low == 0 && !le && ms.eq != len) {
+            le = true;
+            continue;
+        }
+        break;
+    }
+    group_sync(bar, ng);  // the part's stores are visible to the whole group
+    // The two sides in buffer dst: [0, low) and [low, len).
+    const int eqn = ms.eq;
+    bool fin[2];
+    const int so[2] = {0, low}, sl[2] = {low, len - low};
+    if (!le) {
+        fin[0] = false;
+        fin[1] = eqn == len - low;  // the upper side holds only pivot-equal keys (also: all keys equal)
+    } else {
+        fin[0] = true;  // '<=' after a '<' pass that moved nothing: the lower side equals the pivot
+        fin[1] = false;
+    }
+    for (int i = 0; i < 2; ++i)
+        if (sl[i] > 0 && (fin[i] || sl[i] == 1)) copy_out<Tr>(a, l.off + so[i], sl[i], dst, g, ng);
+    if (g == 0) {
+        // The side that needs another split goes below the other.  (The
+        // packing loop reads the stack only between passes.)
+        const int order[2] = {sl[0] > Tr::LEAF ? 0 : 1, sl[0] > Tr::LEAF ? 1 : 0};
+        for (int j = 0; j < 2; ++j) {
+            const int i = order[j];
+            if (sl[i] <= 1 || fin[i]) continue;
+            if (sm.nside >= LeafSmem<Tr>::kSides) {  // never (see LeafSmem::side)
+                set_error(a.ctrl, kErrInternalIndex, 7);
+                continue;
+            }
+            Leaf c;
+            c.off = l.off + so[i];
+            c.len = sl[i];
+            c.flags = dst == 1 ? kLeafScratch : 0;
+            sm.side[sm.nside++] = c;
+        }
+    }
+}
+
 template <class Tr>
 __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K, typename Tr::V> a)
 {
@@ -193,7 +408,10 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
     const long long n_large = static_cast<long long>(ld_relaxed_u64(&c->n_large));
     const long long n_small = static_cast<long long>(ld_relaxed_u64(&c->n_small));
     constexpr int E = LeafCfg<Tr>::E;
-    if (tid == 0) sm.has_carry = 0;
+    if (tid == 0) {
+        sm.has_carry = 0;
+        sm.nside = 0;
+    }
     // Large parts: thread 0 packs parts into thread groups (32 .. kLThreads
     // threads each, a multiple of 32, E keys per thread); a part that does
     // not fit (or finds no named barrier left) is carried over to this CTA's
@@ -207,14 +425,18 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
                 if (sm.has_carry) {
                     l = sm.carry;
                     sm.has_carry = 0;
+                } else if (sm.nside > 0) {
+                    l = sm.side[--sm.nside];  // a side of this CTA's last split: still in L2
                 } else {
                     const long long idx = static_cast<long long>(atomicAdd(&c->claim_large, 1ull));
                     if (idx >= n_large) break;
                     l = a.leaves[idx];
                     if (!leaf_ok<Tr>(a, l, false)) continue;
                 }
+                // A finished run is copied and a mid-range part split by the
+                // whole CTA; a part to sort takes 32*m threads, E keys each.
                 int need = kLThreads;
-                if (!(l.flags & kLeafFinal)) need = 32 * ((l.len + 32 * E - 1) / (32 * E));
+                if (!(l.flags & kLeafFinal) && l.len <= Tr::LEAF) need = 32 * ((l.len + 32 * E - 1) / (32 * E));
                 if (used + need > kLThreads || (need > 32 && nbar == kLeafBarriers)) {
                     sm.carry = l;
                     sm.has_carry = 1;
@@ -237,7 +459,7 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
         if (sm.has_carry) {
             // The part carried over is the next pass's: pull its keys (and
             // values) towards L2 now, so that its loads meet L2 instead of HBM
-            // once this pass's sorts are done (one CTA per SM: nothing else
+            // once this pass's work is done (one CTA per SM: nothing else
             // hides that latency).
             const Leaf nl = sm.carry;
             const int src = (nl.flags & kLeafScratch) ? 1 : 0;
@@ -264,6 +486,16 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
                 for (int i = tid; i < l.len; i += kLThreads) {
                     a.okeys[l.off + i] = gk[i];
                     if constexpr (Tr::KV) a.ovals[l.off + i] = gv[i];
+                }
+            } else if (l.len > Tr::LEAF) {
+                const int st = sm.grp[gi].start;
+                const long long tm0 = (a.profile && tid == st) ? prof_clock() : 0;
+                // Alone in its pass: the group is the whole CTA.
+                mid_split<Tr>(a, l, sm, *reinterpret_cast<MidState *>(keys + st * E), tid - st, sm.grp[gi].nthreads,
+                              sm.grp[gi].bar);
+                if (a.profile && tid == st) {
+                    atomicAdd(&a.ctrl->cycles[29], static_cast<unsigned long long>(prof_clock() - tm0));
+                    atomicAdd(&a.ctrl->cycles[30], 1ull);
                 }
             } else {
                 group_leaf<Tr>(a, l, keys, sm.grp[gi].start, sm.grp[gi].nthreads, sm.grp[gi].bar);
