@@ -14,6 +14,9 @@ template <class Tr, int DriverMin>
 struct Launcher {
     using K = typename Tr::K;
     using V = typename Tr::V;
+    // The leaf kernel depends only on the key kind and the leaf sizes: the
+    // partition tile variants of a kind share one instantiation.
+    using LTr = Traits<K, Tr::KV, 1, Tr::LEAF, Tr::SMALL>;
     static constexpr size_t kDriverSmem = sizeof(DriverSmem<Tr>);
 
     static KernelLimits limits()
@@ -24,7 +27,7 @@ struct Launcher {
         l.small_max = Tr::SMALL;
         l.tile = Tr::T;
         l.driver_smem = kDriverSmem;
-        l.leaf_smem = sizeof(LeafSmem<Tr>) + LeafCfg<Tr>::kDynSmem;
+        l.leaf_smem = sizeof(LeafSmem<LTr>) + LeafCfg<LTr>::kDynSmem;
         return l;
     }
     static int prepare()
@@ -35,8 +38,11 @@ struct Launcher {
             rc = cudaFuncSetAttribute(driver_kernel<Tr, DriverMin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(kDriverSmem));
             if (rc == 0)
-                rc = cudaFuncSetAttribute(leaf_kernel<Tr>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          static_cast<int>(LeafCfg<Tr>::kDynSmem));
+                rc = cudaFuncSetAttribute(leaf_kernel<LTr, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(LeafCfg<LTr>::kDynSmem));
+            if (rc == 0)
+                rc = cudaFuncSetAttribute(leaf_kernel<LTr, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(LeafCfg<LTr>::kDynSmem));
             done = 1;
         }
         return rc;
@@ -48,7 +54,8 @@ struct Launcher {
         if (which == 0)
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, driver_kernel<Tr, DriverMin>, kDThreads,
                                                                  kDriverSmem);
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, leaf_kernel<Tr>, kLThreads, LeafCfg<Tr>::kDynSmem);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, leaf_kernel<LTr, false>, kLThreads,
+                                                             LeafCfg<LTr>::kDynSmem);
     }
     static int launch(const Args<K, V> &a, LaunchCfg &cfg)
     {
@@ -66,7 +73,13 @@ struct Launcher {
         if (a.partition_only || a.seg_off || a.n > a.leaf_max)
             driver_kernel<Tr, DriverMin><<<cfg.grid_driver, kDThreads, kDriverSmem, s>>>(a);
         if (cfg.profile) cudaEventRecord(ev[2], s);
-        if (!a.partition_only) leaf_kernel<Tr><<<cfg.grid_leaf, kLThreads, LeafCfg<Tr>::kDynSmem, s>>>(a);
+        if (!a.partition_only) {
+            // Parts above LEAF are listed only when the threshold allows them.
+            if (a.leaf_max > LTr::LEAF)
+                leaf_kernel<LTr, true><<<cfg.grid_leaf, kLThreads, LeafCfg<LTr>::kDynSmem, s>>>(a);
+            else
+                leaf_kernel<LTr, false><<<cfg.grid_leaf, kLThreads, LeafCfg<LTr>::kDynSmem, s>>>(a);
+        }
         if (cfg.profile) cudaEventRecord(ev[3], s);
         return static_cast<int>(cudaGetLastError());
     }

@@ -98,10 +98,11 @@ struct LeafSmem {
 };
 
 // A listed part must lie inside the array and fit the kernel that takes it.
-template <class Tr>
+template <class Tr, bool MID>
 __device__ bool leaf_ok(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l, bool small)
 {
-    const int64_t cap = (l.flags & kLeafFinal) ? (small ? a.small_max : kCopyChunk) : (small ? a.small_max : Tr::MID);
+    const int64_t cap =
+        (l.flags & kLeafFinal) ? (small ? a.small_max : kCopyChunk) : (small ? a.small_max : (MID ? Tr::MID : Tr::LEAF));
     const bool ok = l.off >= 0 && l.len > 0 && l.len <= cap && l.off + l.len <= a.n;
     if (!ok) set_error(a.ctrl, kErrInternalIndex, 3);
     return ok;
@@ -377,7 +378,10 @@ __device__ __noinline__ void mid_split(const Args<typename Tr::K, typename Tr::V
     }
 }
 
-template <class Tr>
+// MID: the listed parts may exceed LEAF (QS_OPT_LEAF_MAX above it), so the
+// kernel carries the mid-range split; without it the kernel has no trace of
+// the stage (the split's call would cost registers around it).
+template <class Tr, bool MID>
 __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K, typename Tr::V> a)
 {
     using K = typename Tr::K;
@@ -431,12 +435,12 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
                     const long long idx = static_cast<long long>(atomicAdd(&c->claim_large, 1ull));
                     if (idx >= n_large) break;
                     l = a.leaves[idx];
-                    if (!leaf_ok<Tr>(a, l, false)) continue;
+                    if (!leaf_ok<Tr, MID>(a, l, false)) continue;
                 }
                 // A finished run is copied and a mid-range part split by the
                 // whole CTA; a part to sort takes 32*m threads, E keys each.
                 int need = kLThreads;
-                if (!(l.flags & kLeafFinal) && l.len <= Tr::LEAF) need = 32 * ((l.len + 32 * E - 1) / (32 * E));
+                if (!(l.flags & kLeafFinal) && (!MID || l.len <= Tr::LEAF)) need = 32 * ((l.len + 32 * E - 1) / (32 * E));
                 if (used + need > kLThreads || (need > 32 && nbar == kLeafBarriers)) {
                     sm.carry = l;
                     sm.has_carry = 1;
@@ -487,7 +491,7 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
                     a.okeys[l.off + i] = gk[i];
                     if constexpr (Tr::KV) a.ovals[l.off + i] = gv[i];
                 }
-            } else if (l.len > Tr::LEAF) {
+            } else if (MID && l.len > Tr::LEAF) {
                 const int st = sm.grp[gi].start;
                 const long long tm0 = (a.profile && tid == st) ? prof_clock() : 0;
                 // Alone in its pass: the group is the whole CTA.
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
             l.off = __shfl_sync(0xffffffffu, mine.off, q);
             l.len = __shfl_sync(0xffffffffu, mine.len, q);
             l.flags = __shfl_sync(0xffffffffu, mine.flags, q);
-            if (!leaf_ok<Tr>(a, l, true)) continue;
+            if (!leaf_ok<Tr, MID>(a, l, true)) continue;
             if (l.flags & kLeafFinal) {
                 const int src = (l.flags & kLeafScratch) ? 1 : 0;
                 for (int i = lane; i < l.len; i += 32) {
