@@ -77,9 +77,13 @@ typedef enum { QS_KIND_I32 = 0, QS_KIND_F64 = 1, QS_KIND_KV = 2 } qs_kind;
  * returned left_w), in [0, n].  The order inside each side is fixed: the lower
  * side keeps input order, the upper side holds its keys in reverse input
  * order.  For kv, d_vals[i] moves with d_keys[i].
- * The kernel partitions out of place into the workspace scratch (one read and
- * one write of each element) and copies the result back into d_keys/d_vals.
- * Returns a negative qs_status on error.
+ * One pass reads every element once: the lower side is written in place
+ * (a tile's lower-side keys only land on positions that this tile or an
+ * earlier one has already read), the upper side into the workspace scratch,
+ * from where it is copied back into d_keys/d_vals once the split is known
+ * (2 * n + 2 * (n - split) element moves in all).  Returns a negative
+ * qs_status on error; after a device-side failure the contents of
+ * d_keys/d_vals are unspecified (keys may be duplicated or lost).
  */
 int64_t qs_partition_i32(int32_t *d_keys, int64_t n, int32_t pivot, qs_stream_t stream);
 int64_t qs_partition_f64(double *d_keys, int64_t n, double pivot, qs_stream_t stream);

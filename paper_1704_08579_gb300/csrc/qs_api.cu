@@ -555,12 +555,17 @@ int64_t run(int kind, K *keys, int32_t *vals, int64_t n, uint64_t pivot_bits, in
     if (partition_only) {
         // Its CTAs left without clearing the look-back words they used.
         w.dirty_words = static_cast<int64_t>(w.h_ctrl->pool_cursor);
-        // The split is known; move the partitioned data back into the caller's arrays.
+        // The split is known.  The lower side was written in place; move the
+        // upper side, [lt, n), back from scratch into the caller's arrays.
         if (cfg.profile) cudaEventRecord(w.ev[4], s);
-        if ((e = cudaMemcpyAsync(keys, w.scratch_k, static_cast<size_t>(n) * sizeof(K), cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        const size_t hi = static_cast<size_t>(n) - static_cast<size_t>(lt);
+        if (lt > static_cast<unsigned long long>(n)) return fail(QS_ERR_INTERNAL, "split beyond the array");
+        if (hi && (e = cudaMemcpyAsync(keys + lt, static_cast<K *>(w.scratch_k) + lt, hi * sizeof(K),
+                                       cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return cuda_fail(e, "cudaMemcpyAsync(copy-back)");
-        if (kind == QS_KIND_KV &&
-            (e = cudaMemcpyAsync(vals, w.scratch_v, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        if (hi && kind == QS_KIND_KV &&
+            (e = cudaMemcpyAsync(vals + lt, static_cast<int32_t *>(w.scratch_v) + lt, hi * 4, cudaMemcpyDeviceToDevice,
+                                 s)) != cudaSuccess)
             return cuda_fail(e, "cudaMemcpyAsync(copy-back)");
         if (cfg.profile) cudaEventRecord(w.ev[5], s);
         if ((e = mark_done(w, s)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");

@@ -846,12 +846,19 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     // Lower side: [off + excl, +L); upper side (reverse order) ends at
     // end - 1 - hpre, where hpre = upper-side keys placed before this tile
     // (ordered: those of the earlier tiles).
+    // A partition-only call writes its lower side in place, into the buffer
+    // it reads: with ordered placement a tile's lower-side keys land at or
+    // before the end of its own window, in windows that have been read
+    // already (this tile's, and earlier tiles' -- its look-back finished only
+    // after every earlier tile published a count, which each tile does only
+    // once its keys are loaded).  Only the upper side goes through scratch.
     const int64_t hpre = a.ordered ? (vstart - off) - excl : sm.hexcl;
     const int H = nvalid - L;
     if (excl >= 0 && off + excl + L <= end && hpre >= 0 && hpre + H <= w.len) {
-        K *__restrict__ lo_k = a.keys[w.src ^ 1] + (off + excl);
+        const int lo_buf = a.partition_only ? w.src : (w.src ^ 1);
+        K *__restrict__ lo_k = a.keys[lo_buf] + (off + excl);
         K *__restrict__ hi_k = a.keys[w.src ^ 1] + (end - 1 - hpre + L);  // key s >= L goes to hi_k - s
-        V *__restrict__ lo_v = a.vals[w.src ^ 1] + (off + excl);
+        V *__restrict__ lo_v = a.vals[lo_buf] + (off + excl);
         V *__restrict__ hi_v = a.vals[w.src ^ 1] + (end - 1 - hpre + L);
         for (int s = tid; s < nvalid; s += kDThreads) {
             const bool lo = s < L;

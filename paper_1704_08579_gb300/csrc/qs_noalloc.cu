@@ -130,8 +130,12 @@ extern "C" int64_t qs_partition_i32_noalloc(int32_t *d_keys, int64_t n, int32_t 
         cudaStreamSynchronize(s) != cudaSuccess)
         return fail(QS_ERR_CUDA, "reading the result failed");
     if (h.status != 0) return fail(h.status, "device-side failure (see qs_status)");
-    if (cudaMemcpyAsync(d_keys, a.keys[1], static_cast<size_t>(n) * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
+    // The lower side was written in place; the upper side, [split, n), comes back from scratch.
+    const int64_t lt = static_cast<int64_t>(h.lt_result);
+    if (lt < 0 || lt > n) return fail(QS_ERR_INTERNAL, "split beyond the array");
+    if (lt < n && (cudaMemcpyAsync(d_keys + lt, a.keys[1] + lt, static_cast<size_t>(n - lt) * 4, cudaMemcpyDeviceToDevice,
+                                   s) != cudaSuccess ||
+                   cudaStreamSynchronize(s) != cudaSuccess))
         return fail(QS_ERR_CUDA, "copy-back failed");
-    return static_cast<int64_t>(h.lt_result);
+    return lt;
 }
