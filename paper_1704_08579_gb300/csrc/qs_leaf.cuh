@@ -146,10 +146,33 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     group_sync(bar, nthreads);
     typename Tr::K *ok = a.okeys + l.off;
     typename Tr::V *ov = a.ovals + l.off;
+    if constexpr (!Tr::KV) {
+        // 16-byte stores from the first 16-byte boundary on (the keys before it
+        // and after the last one one by one): fewer, wider writes, which also
+        // carry better over the host link when the output is mapped host memory.
+        using K = typename Tr::K;
+        constexpr int VWS = 16 / static_cast<int>(sizeof(K));
+        const int head = static_cast<int>((16 - (reinterpret_cast<uintptr_t>(ok) & 15)) & 15) / static_cast<int>(sizeof(K));
+        const int h = head < len ? head : len;
+        const int nvec = (len - h) / VWS;
+        const int tail0 = h + nvec * VWS;
+        for (int q = g; q < nvec; q += nthreads) {
+            K v[VWS];
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int i = g + r * nthreads;
-        if (i < len) LK::store(ok, ov, i, gs[swz<E>(i)]);
+            for (int j = 0; j < VWS; ++j) LK::store(v, ov, j, gs[swz<E>(h + q * VWS + j)]);
+            if constexpr (VWS == 2)
+                *reinterpret_cast<double2 *>(ok + h + q * VWS) = make_double2(v[0], v[1]);
+            else
+                *reinterpret_cast<int4 *>(ok + h + q * VWS) = make_int4(v[0], v[1], v[2], v[3]);
+        }
+        if (g < h) LK::store(ok, ov, g, gs[swz<E>(g)]);
+        if (tail0 + g < len) LK::store(ok, ov, tail0 + g, gs[swz<E>(tail0 + g)]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int i = g + r * nthreads;
+            if (i < len) LK::store(ok, ov, i, gs[swz<E>(i)]);
+        }
     }
     if (a.profile && g == 0) atomicAdd(&a.ctrl->cycles[23], static_cast<unsigned long long>(prof_clock() - t0));
 }
