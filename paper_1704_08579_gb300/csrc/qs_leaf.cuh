@@ -146,24 +146,30 @@ __device__ void group_leaf(const Args<typename Tr::K, typename Tr::V> &a, const 
     group_sync(bar, nthreads);
     typename Tr::K *ok = a.okeys + l.off;
     typename Tr::V *ov = a.ovals + l.off;
-    if constexpr (!Tr::KV) {
-        // 16-byte stores from the first 16-byte boundary on (the keys before it
-        // and after the last one one by one): fewer, wider writes, which also
-        // carry better over the host link when the output is mapped host memory.
-        using K = typename Tr::K;
+    // 16-byte stores from the first 16-byte boundary on (the keys before it
+    // and after the last one one by one): fewer, wider writes, which also
+    // carry better over the host link when the output is mapped host memory.
+    // Key/value parts need both arrays in the same 16-byte phase.
+    using K = typename Tr::K;
+    using V = typename Tr::V;
+    const uintptr_t kph = reinterpret_cast<uintptr_t>(ok) & 15;
+    if (!Tr::KV || kph == (reinterpret_cast<uintptr_t>(ov) & 15)) {
         constexpr int VWS = 16 / static_cast<int>(sizeof(K));
-        const int head = static_cast<int>((16 - (reinterpret_cast<uintptr_t>(ok) & 15)) & 15) / static_cast<int>(sizeof(K));
+        const int head = static_cast<int>((16 - kph) & 15) / static_cast<int>(sizeof(K));
         const int h = head < len ? head : len;
         const int nvec = (len - h) / VWS;
         const int tail0 = h + nvec * VWS;
         for (int q = g; q < nvec; q += nthreads) {
-            K v[VWS];
+            K kv[VWS];
+            V vv[VWS];
 #pragma unroll
-            for (int j = 0; j < VWS; ++j) LK::store(v, ov, j, gs[swz<E>(h + q * VWS + j)]);
-            if constexpr (VWS == 2)
-                *reinterpret_cast<double2 *>(ok + h + q * VWS) = make_double2(v[0], v[1]);
-            else
-                *reinterpret_cast<int4 *>(ok + h + q * VWS) = make_int4(v[0], v[1], v[2], v[3]);
+            for (int j = 0; j < VWS; ++j) LK::store(kv, vv, j, gs[swz<E>(h + q * VWS + j)]);
+            if constexpr (VWS == 2) {
+                *reinterpret_cast<double2 *>(ok + h + q * VWS) = make_double2(kv[0], kv[1]);
+            } else {
+                *reinterpret_cast<int4 *>(ok + h + q * VWS) = make_int4(kv[0], kv[1], kv[2], kv[3]);
+                if constexpr (Tr::KV) *reinterpret_cast<int4 *>(ov + h + q * VWS) = make_int4(vv[0], vv[1], vv[2], vv[3]);
+            }
         }
         if (g < h) LK::store(ok, ov, g, gs[swz<E>(g)]);
         if (tail0 + g < len) LK::store(ok, ov, tail0 + g, gs[swz<E>(tail0 + g)]);
