@@ -2,6 +2,7 @@
 point that include/qs.h declares, and its host-side argument checks return the
 documented status codes.  No call here reaches a kernel."""
 import ctypes
+import os
 
 import pytest
 
@@ -103,3 +104,27 @@ def test_binding_rejects_bad_dtypes():
     torch = pytest.importorskip("torch")
     with pytest.raises(TypeError):
         qs.sort(torch.zeros(4, dtype=torch.float32))
+
+
+def test_stats_layout_matches_header(tmp_path):
+    """The binding's qs_stats mirror has the header's size and field offsets
+    (qs_get_stats writes sizeof(qs_stats) bytes into the caller's struct)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = [name for name, _ in qs.Stats._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"qs.h\"\nint main(void) {\n"
+                   "  printf(\"size %zu\\n\", sizeof(qs_stats));\n"
+                   + "".join("  printf(\"%s %%zu\\n\", offsetof(qs_stats, %s));\n" % (f, f) for f in fields)
+                   + "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(qs.HEADER), str(src), "-o", str(exe)], check=True)
+    out = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                         text=True).stdout.splitlines())
+    assert int(out["size"]) == ctypes.sizeof(qs.Stats)
+    for f in fields:
+        assert int(out[f]) == getattr(qs.Stats, f).offset, f
