@@ -65,7 +65,9 @@ struct LeafCfg {
     using S = typename LeafKey<Tr>::S;
     static constexpr int E = sizeof(S) == 8 ? 16 : 32;
     static_assert(kLThreads * E == Tr::LEAF, "a CTA holds exactly one largest leaf");
-    static constexpr size_t kDynSmem = sizeof(S) * Tr::LEAF;  // the keys, in dynamic shared memory
+    // The keys, in dynamic shared memory (+64 bytes: a mid-range split shifts
+    // each chunk it copies in to the chunk's 16-byte phase).
+    static constexpr size_t kDynSmem = sizeof(S) * Tr::LEAF + 64;
 };
 
 struct LeafGroup {
@@ -78,6 +80,13 @@ struct LeafGroup {
 // Named barriers 1..15 are available to groups (barrier 0 is __syncthreads).
 constexpr int kLeafBarriers = 15;
 
+
+// State of the CTA's mid-range split (one at a time).
+struct MidState {
+    unsigned tot[2][32];  // per warp: lower-side keys | valid keys << 16 (two chunks in flight)
+    uint64_t pivot;       // the pivot's raw bits
+    int eq;               // pivot-equal keys of the part
+};
 
 template <class Tr>
 struct LeafSmem {
@@ -95,6 +104,9 @@ struct LeafSmem {
     static constexpr int kSides = 8;
     Leaf side[kSides];
     int nside;
+    MidState mid;
+    alignas(8) unsigned long long mbar;  // completion of a split chunk's bulk copy
+    uint32_t mbar_par;                   // parity of its next phase
 };
 
 // A listed part must lie inside the array and fit the kernel that takes it.
@@ -232,49 +244,95 @@ __device__ void copy_out(const Args<typename Tr::K, typename Tr::V> &a, int64_t 
     }
 }
 
-// Per-group state of a mid-range split, kept at the start of the group's own
-// slice of the leaf kernel's shared memory (a split sorts nothing there).
-struct MidState {
-    unsigned tot[2][32];  // per warp: lower-side keys | valid keys << 16 (two chunks in flight)
-    uint64_t pivot;       // the pivot's raw bits
-    int eq;               // pivot-equal keys of the part
-};
-static_assert(sizeof(MidState) <= 64 * 16 * 4, "fits the smallest split group's slice");
-
-// One quicksort step of a mid-range part by a group of ng threads (thread g,
-// named barrier `bar`; the packing loop gives it the whole CTA, alone in its
-// pass).  The pivot is the median of 64 sampled keys.  A chunk of ng*E keys at a
-// time is loaded (thread g takes keys g, g + ng, ...), compared, and ranked
-// with warp ballots: within a warp, the lower-side keys of a round take
-// consecutive slots; across the group's warps, a scan of the per-warp
-// totals.  Keys are written straight to the other buffer: lower side forward
-// from the part's start, upper side backward from its end (the two write
-// cursors of Section III-B); the sides are sorted next, so the order inside
-// them is free.  Equal keys as in the device-wide pass: if nothing is below
-// the pivot the pass is repeated with '<=', whose lower side holds only
-// pivot-equal keys and is finished; a side of only pivot-equal keys is
-// finished too.  Finished sides are copied to the output at once; the others
-// are left on sm.side for the packing loop.
+// One quicksort step of a mid-range part by the whole CTA (the packing loop
+// gives it every thread, alone in its pass; g = threadIdx.x, named barrier
+// `bar`).  The pivot is the median of 64 sampled keys.  A chunk of
+// kLThreads*E keys at a time is brought into shared memory (the `smem`
+// buffer) by a TMA bulk copy of its 16-byte aligned body, placed at the
+// chunk's own 16-byte phase so that any alignment works (the few keys
+// outside the body are read from global memory directly); the next chunk's
+// copy is issued as soon as the current one has been read, so it lands while
+// the current one is placed.  Each thread takes keys g, g + kLThreads, ...,
+// compares them, and ranks them with warp ballots: within a warp, the
+// lower-side keys of a round take consecutive slots; across warps, a scan of
+// the per-warp totals.  Keys are written straight to the other buffer: lower
+// side forward from the part's start, upper side backward from its end (the
+// two write cursors of Section III-B); the sides are sorted next, so the
+// order inside them is free.  Equal keys as in the device-wide pass: if
+// nothing is below the pivot the pass is repeated with '<=', whose lower side
+// holds only pivot-equal keys and is finished; a side of only pivot-equal
+// keys is finished too.  Finished sides are copied to the output at once;
+// the others are left on sm.side for the packing loop.
 template <class Tr>
 __device__ __noinline__ void mid_split(const Args<typename Tr::K, typename Tr::V> &a, const Leaf &l, LeafSmem<Tr> &sm,
-                                       MidState &ms, int g, int ng, int bar)
+                                       unsigned char *smem, int bar)
 {
     using K = typename Tr::K;
     using V = typename Tr::V;
     using Ops = KeyOps<K>;
     using S = typename Ops::S;
     constexpr int E = LeafCfg<Tr>::E;  // keys per thread and chunk
-    const int lane = g & 31, gw = g >> 5, nw = ng >> 5;
+    constexpr int ng = kLThreads, nw = kLThreads / 32, chunk = kLThreads * E;
+    constexpr int VK = 16 / static_cast<int>(sizeof(K)), VV = 16 / static_cast<int>(sizeof(V));
+    constexpr size_t kVOff = ((static_cast<size_t>(chunk) + VK) * sizeof(K) + 15) & ~static_cast<size_t>(15);
+    static_assert(kVOff + (Tr::KV ? (static_cast<size_t>(chunk) + VV) * sizeof(V) : 0) <= LeafCfg<Tr>::kDynSmem,
+                  "a chunk and its alignment shift fit the leaf kernel's dynamic shared memory");
+    const int g = threadIdx.x;
+    const int lane = g & 31, gw = g >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
+    MidState &ms = sm.mid;
     const int src = (l.flags & kLeafScratch) ? 1 : 0, dst = src ^ 1;
     const int len = l.len;
     const K *gk = a.keys[src] + l.off;
     const V *gv = a.vals[src] + l.off;
     K *dk = a.keys[dst] + l.off;
     V *dv = a.vals[dst] + l.off;
+    K *sk = reinterpret_cast<K *>(smem);
+    V *sv = reinterpret_cast<V *>(smem + kVOff);
     const bool lead = a.profile && g == 0;
     const long long tq = lead ? prof_clock() : 0;
-    if (gw == 0) {
+    // Layout of chunk c0 (every thread computes the same): element i of the
+    // chunk sits at sk[pk + i]; [hk, bk) is the body the bulk copy brings
+    // (empty if an address check fails: then every key is read directly).
+    struct Lay {
+        int pk, hk, bk, pv, hv, bv;
+        uint32_t bytes;
+    };
+    auto layout = [&](int c0) {
+        Lay y;
+        const int nv = len - c0 < chunk ? len - c0 : chunk;
+        y.pk = static_cast<int>((reinterpret_cast<uintptr_t>(gk + c0) & 15) / sizeof(K));
+        y.hk = (VK - y.pk) % VK;
+        if (y.hk > nv) y.hk = nv;
+        y.bk = y.hk + (nv - y.hk) / VK * VK;
+        const uintptr_t ks = reinterpret_cast<uintptr_t>(gk + c0 + y.hk);
+        if (((ks | static_cast<uintptr_t>(smem_addr(sk + y.pk + y.hk))) & 15) != 0) y.bk = y.hk;
+        y.bytes = static_cast<uint32_t>((y.bk - y.hk) * sizeof(K));
+        y.pv = y.hv = y.bv = 0;
+        if constexpr (Tr::KV) {
+            y.pv = static_cast<int>((reinterpret_cast<uintptr_t>(gv + c0) & 15) / sizeof(V));
+            y.hv = (VV - y.pv) % VV;
+            if (y.hv > nv) y.hv = nv;
+            y.bv = y.hv + (nv - y.hv) / VV * VV;
+            const uintptr_t vs = reinterpret_cast<uintptr_t>(gv + c0 + y.hv);
+            if (((vs | static_cast<uintptr_t>(smem_addr(sv + y.pv + y.hv))) & 15) != 0) y.bv = y.hv;
+            y.bytes += static_cast<uint32_t>((y.bv - y.hv) * sizeof(V));
+        }
+        return y;
+    };
+    auto issue = [&](int c0) {  // thread 0: the bulk copies of chunk c0's bodies
+        const Lay y = layout(c0);
+        if (y.bytes == 0) return;
+        mbar_arrive_expect_tx(&sm.mbar, y.bytes);
+        if (y.bk > y.hk)
+            bulk_g2s(sk + y.pk + y.hk, gk + c0 + y.hk, static_cast<uint32_t>((y.bk - y.hk) * sizeof(K)), &sm.mbar);
+        if constexpr (Tr::KV)
+            if (y.bv > y.hv)
+                bulk_g2s(sv + y.pv + y.hv, gv + c0 + y.hv, static_cast<uint32_t>((y.bv - y.hv) * sizeof(V)), &sm.mbar);
+    };
+    uint32_t mpar = sm.mbar_par;
+    if (g == 0) issue(0);
+    if (gw == 0) {  // the pivot sample's loads overlap the first chunk's copy
         const uint64_t pb =
             sample_median<K>(a.keys[src], l.off, len, static_cast<uint64_t>(l.off) * 0x9E3779B97F4A7C15ull + len);
         if (lane == 0) {
@@ -286,7 +344,6 @@ __device__ __noinline__ void mid_split(const Args<typename Tr::K, typename Tr::V
     group_sync(bar, ng);
     if (lead) atomicAdd(&a.ctrl->cycles[31], static_cast<unsigned long long>(prof_clock() - tq));
     const S ps = s_of_bits<K>(ms.pivot);
-    const int chunk = ng * E;
     bool le = false;  // '<' first
     int low = 0, par = 0;
     for (;;) {
@@ -295,14 +352,22 @@ __device__ __noinline__ void mid_split(const Args<typename Tr::K, typename Tr::V
         for (int c0 = 0; c0 < len; c0 += chunk, par ^= 1) {
             long long tc = lead ? prof_clock() : 0;
             const int nv = len - c0 < chunk ? len - c0 : chunk;
+            if (le && c0 == 0 && g == 0) issue(0);  // the '<=' pass reads the part again
+            const Lay y = layout(c0);
+            if (y.bytes) {  // CTA-uniform; a copy that was issued always lands, so a late one is waited out
+                if (!mbar_wait_bounded(&sm.mbar, mpar, a.ctrl, a.wait_limit_ns))
+                    mbar_wait_bounded(&sm.mbar, mpar, a.ctrl, kDrainFloorNs);
+                mpar ^= 1u;
+            }
             K k[E];
             V v[Tr::KV ? E : 1];
 #pragma unroll
             for (int r = 0; r < E; ++r) {
                 const int i = r * ng + g;
-                k[r] = i < nv ? __ldcg(gk + c0 + i) : K(0);
-                if constexpr (Tr::KV) v[r] = i < nv ? __ldcg(gv + c0 + i) : 0;
+                k[r] = i < nv ? ((i >= y.hk && i < y.bk) ? sk[y.pk + i] : __ldcg(gk + c0 + i)) : K(0);
+                if constexpr (Tr::KV) v[r] = i < nv ? ((i >= y.hv && i < y.bv) ? sv[y.pv + i] : __ldcg(gv + c0 + i)) : 0;
             }
+            fence_proxy_async_smem();  // these reads, before a later bulk copy overwrites the buffer
             // This warp's lower-side, valid and pivot-equal keys.
             int wl = 0, wv = 0, eq = 0;
 #pragma unroll
@@ -327,6 +392,8 @@ __device__ __noinline__ void mid_split(const Args<typename Tr::K, typename Tr::V
                 tc = now;
             }
             group_sync(bar, ng);
+            // Every thread has read this chunk: bring the next one meanwhile.
+            if (g == 0 && c0 + chunk < len) issue(c0 + chunk);
             if (lead) {
                 const long long now = prof_clock();
                 atomicAdd(&a.ctrl->cycles[33], static_cast<unsigned long long>(now - tc));
@@ -374,6 +441,7 @@ __device__ __noinline__ void mid_split(const Args<typename Tr::K, typename Tr::V
         break;
     }
     group_sync(bar, ng);  // the part's stores are visible to the whole group
+    if (g == 0) sm.mbar_par = mpar;
     // The two sides in buffer dst: [0, low) and [low, len).
     const int eqn = ms.eq;
     bool fin[2];
@@ -444,6 +512,11 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
     if (tid == 0) {
         sm.has_carry = 0;
         sm.nside = 0;
+        if constexpr (MID) {
+            mbar_init(&sm.mbar, 1);
+            fence_mbar_init();
+            sm.mbar_par = 0;
+        }
     }
     // Large parts: thread 0 packs parts into thread groups (32 .. kLThreads
     // threads each, a multiple of 32, E keys per thread); a part that does
@@ -524,8 +597,7 @@ __global__ void __launch_bounds__(kLThreads, 1) leaf_kernel(Args<typename Tr::K,
                 const int st = sm.grp[gi].start;
                 const long long tm0 = (a.profile && tid == st) ? prof_clock() : 0;
                 // Alone in its pass: the group is the whole CTA.
-                mid_split<Tr>(a, l, sm, *reinterpret_cast<MidState *>(keys + st * E), tid - st, sm.grp[gi].nthreads,
-                              sm.grp[gi].bar);
+                mid_split<Tr>(a, l, sm, leaf_dyn, sm.grp[gi].bar);
                 if (a.profile && tid == st) {
                     atomicAdd(&a.ctrl->cycles[29], static_cast<unsigned long long>(prof_clock() - tm0));
                     atomicAdd(&a.ctrl->cycles[30], 1ull);
