@@ -141,6 +141,10 @@ int qs_sort_segmented_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, const int6
  *      comes out larger than 4x its even share is simply split further by the
  *      plain sampled-median pivots: that is the fallback, and qs_stats reports
  *      bucket_max / bucket_over as the measure of the model.
+ * With QS_OPT_BUCKET_LEVELS = 2 a second 256-way bucket pass runs inside
+ * every bucket first (its 255 splitters sampled from the bucket itself:
+ * 1024 keys, every 4th of them sorted), and step 4 sorts the 65,536
+ * sub-buckets -- most of them small enough for the leaf kernel alone.
  * The sorted output is the same as qs_sort_*'s (keys bit for bit).
  *
  * d_params: device float array of qs_mlp_param_count() parameters laid out as
@@ -368,6 +372,11 @@ int qs_get_stats(qs_stats *out);
  *   QS_OPT_SYNC          1: qs_sort_* and qs_sort_segmented_* return only
  *                        after their work has finished, with its status;
  *                        0 (default): they are asynchronous.
+ *   QS_OPT_BUCKET_LEVELS qs_sort_learned_*: 1 = one 256-way bucket pass, the
+ *                        plain method inside each bucket; 2 = a second
+ *                        256-way pass inside every bucket, then the plain
+ *                        method inside each of the 65,536 sub-buckets;
+ *                        0 = the default (2).
  * The tuning options are what the autotuner (paper_1704_08579_gb300.autotune)
  * searches.
  */
@@ -380,7 +389,8 @@ enum {
     QS_OPT_SMALL_MAX = 6,
     QS_OPT_DRIVER_ITEMS = 7,
     QS_OPT_ORDERED = 8,
-    QS_OPT_SYNC = 9
+    QS_OPT_SYNC = 9,
+    QS_OPT_BUCKET_LEVELS = 10
 };
 int qs_set_option(int option, int64_t value);
 /* Current value of an option (as set, 0 = the default) into *value; returns

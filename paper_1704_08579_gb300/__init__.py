@@ -37,7 +37,7 @@ STATUS = {
 }
 KIND = {"i32": 0, "f64": 1, "kv": 2}
 OPTION = {"profile": 1, "wait_limit_ns": 2, "task_cap": 3, "driver_ctas": 4, "leaf_max": 5, "small_max": 6,
-          "driver_items": 7, "ordered": 8, "sync": 9}
+          "driver_items": 7, "ordered": 8, "sync": 9, "bucket_levels": 10}
 
 _lib = None
 _lock = threading.Lock()

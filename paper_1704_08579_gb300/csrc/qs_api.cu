@@ -31,6 +31,7 @@ std::atomic<int64_t> g_small_max{0};  // 0 = the kind's compiled maximum
 std::atomic<int64_t> g_driver_items{0};  // 0 = the kind's default partition tile
 std::atomic<int> g_ordered{0};  // 1 = the sort's partitions place tiles in input order too
 std::atomic<int> g_sync{0};     // 1 = sorts return only after their work has finished
+std::atomic<int> g_bucket_levels{0};  // learned / sampled sorts: 1 or 2 bucket levels, 0 = the default (2)
 
 constexpr int64_t kMaxN = 1ll << 38;
 
@@ -81,6 +82,8 @@ struct Workspace {
     int64_t last_grid_driver = 0, last_grid_leaf = 0, last_n = 0, last_kind = 0;
     cudaStream_t capture = nullptr;  // private stream used to capture CUDA graphs
     void *aux = nullptr;                   // learned-splitter / bucket state
+    void *cnt2 = nullptr;                  // second bucket level: per-chunk sub-bucket counts
+    size_t cnt2_bytes = 0;
     LearnedState *h_learned = nullptr;     // pinned copy of its state
     struct Graph {
         std::string key;
@@ -261,9 +264,11 @@ void ws_free(Workspace &w)
     drop_graphs(w);
     if (w.capture) cudaStreamDestroy(w.capture);
     w.capture = nullptr;
-    void *bufs[] = {w.scratch_k, w.scratch_v, w.stage_k, w.stage_v, w.tasks, w.owner, w.pool, w.leaves, w.ctrl, w.aux};
+    void *bufs[] = {w.scratch_k, w.scratch_v, w.stage_k, w.stage_v, w.tasks, w.owner, w.pool, w.leaves, w.ctrl, w.aux, w.cnt2};
     if (w.h_learned) cudaFreeHost(w.h_learned);
     w.aux = nullptr;
+    w.cnt2 = nullptr;
+    w.cnt2_bytes = 0;
     w.h_learned = nullptr;
     for (void *p : bufs)
         if (p) cudaFree(p);
@@ -651,7 +656,10 @@ int run_host(int kind, K *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream
 
 constexpr size_t kAuxState = 4096, kAuxSketch = 4096, kAuxSample = 8192, kAuxSpl = 4096;
 constexpr size_t kAuxCnt = sizeof(int64_t) * kLearnedBuckets * kMaxBucketCtas, kAuxAct = 4096;
-constexpr size_t kAuxBytes = kAuxState + kAuxSketch + kAuxSample + kAuxSpl + kAuxCnt + kAuxAct;
+constexpr size_t kAuxSpl2 = sizeof(uint64_t) * kLearnedBuckets2;
+constexpr size_t kAuxOff2 = (sizeof(int64_t) * (kLearnedBuckets2 + 1) + 4095) / 4096 * 4096, kAuxCbase = 4096;
+constexpr size_t kAuxBytes =
+    kAuxState + kAuxSketch + kAuxSample + kAuxSpl + kAuxCnt + kAuxAct + kAuxSpl2 + kAuxOff2 + kAuxCbase;
 
 int aux_ensure(Workspace &w)
 {
@@ -677,6 +685,11 @@ LearnedPtrs aux_ptrs(Workspace &w)
     p.splitters = b + kAuxState + kAuxSketch + kAuxSample;
     p.cnt = reinterpret_cast<int64_t *>(b + kAuxState + kAuxSketch + kAuxSample + kAuxSpl);
     p.act = reinterpret_cast<float *>(b + kAuxState + kAuxSketch + kAuxSample + kAuxSpl + kAuxCnt);
+    char *l2 = b + kAuxState + kAuxSketch + kAuxSample + kAuxSpl + kAuxCnt + kAuxAct;
+    p.spl2 = l2;
+    p.off2 = reinterpret_cast<int64_t *>(l2 + kAuxSpl2);
+    p.cbase = reinterpret_cast<int64_t *>(l2 + kAuxSpl2 + kAuxOff2);
+    p.cnt2 = static_cast<int64_t *>(w.cnt2);
     return p;
 }
 
@@ -715,9 +728,15 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     if (dev < 0 || dev >= kMaxDevices) return fail(QS_ERR_INVALID_ARG, "device %d out of range", dev);
     Workspace &w = *workspace_for(dev);
     std::lock_guard<std::mutex> guard(w.mu);
-    int rc = ws_ensure(w, n, kind, kLearnedBuckets);
+    const int levels = op == kOpSortLearned ? (g_bucket_levels.load() == 1 ? 1 : 2) : 1;
+    const int64_t ctas2 = n / kBucket2Chunk + kLearnedBuckets + 1;  // >= the sum over buckets of ceil(size / chunk)
+    int rc = ws_ensure(w, n, kind, levels == 2 ? kLearnedBuckets2 : kLearnedBuckets);
     if (rc) return rc;
     if ((rc = aux_ensure(w))) return rc;
+    if (levels == 2 &&
+        (rc = grow(&w.cnt2, &w.cnt2_bytes, static_cast<size_t>(ctas2) * kLearnedBuckets * sizeof(int64_t),
+                   "second-level bucket counts")))
+        return rc;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if ((rc = check_earlier(w, s))) return rc;
     if ((e = order_after_previous(w, s)) != cudaSuccess) return cuda_fail(e, "cudaStreamWaitEvent");
@@ -731,6 +750,8 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     lc.user_spl = user_spl;
     lc.nsplit = nsplit;
     lc.ctas = w.sms * 4 < kMaxBucketCtas ? w.sms * 4 : kMaxBucketCtas;
+    lc.levels = levels;
+    lc.ctas2 = static_cast<int>(ctas2);
     lc.bound = 4 * (n / kLearnedBuckets + 1);
     lc.sketch_out = sketch_out;
     lc.minmax_out = minmax_out;
@@ -1022,6 +1043,10 @@ int qs_set_option(int option, int64_t value)
         if (value < 0 || value > 1) return QS_ERR_INVALID_ARG;
         g_sync = static_cast<int>(value);
         return QS_OK;
+    case QS_OPT_BUCKET_LEVELS:
+        if (value < 0 || value > 2) return QS_ERR_INVALID_ARG;
+        g_bucket_levels = static_cast<int>(value);
+        return QS_OK;
     case QS_OPT_LEAF_MAX:
     case QS_OPT_SMALL_MAX:
         if (value < 0 || (value > 0 && (value < 32 || (value & (value - 1))))) return QS_ERR_INVALID_ARG;
@@ -1045,6 +1070,7 @@ int qs_get_option(int option, int64_t *value)
     case QS_OPT_DRIVER_ITEMS: *value = g_driver_items.load(); return QS_OK;
     case QS_OPT_ORDERED: *value = g_ordered.load(); return QS_OK;
     case QS_OPT_SYNC: *value = g_sync.load(); return QS_OK;
+    case QS_OPT_BUCKET_LEVELS: *value = g_bucket_levels.load(); return QS_OK;
     default: return QS_ERR_INVALID_ARG;
     }
 }

@@ -132,6 +132,10 @@ struct LaunchCfg {
 constexpr int kLearnedBuckets = 256;
 constexpr int kLearnedSketch = 1024;
 constexpr int kMaxBucketCtas = 2048;
+// Second bucket level: every first-level bucket split 256 ways again, by its
+// own sampled splitters; its passes give each CTA one chunk of one bucket.
+constexpr int kLearnedBuckets2 = kLearnedBuckets * kLearnedBuckets;
+constexpr int64_t kBucket2Chunk = 1 << 16;
 struct alignas(128) LearnedState {
     double minmax[2];
     int64_t bucket_off[kLearnedBuckets + 1];  // bucket starts + total (nsplit + 2 used)
@@ -148,6 +152,11 @@ struct LearnedPtrs {
     void *splitters;   // 255 sort-space keys (8 bytes each)
     int64_t *cnt;      // kLearnedBuckets x kMaxBucketCtas
     float *act;        // one sample's MLP activations
+    // Second level (sorts with two bucket levels):
+    void *spl2;        // kLearnedBuckets x 256 sort-space keys: each bucket's 255 sorted sub-splitters
+    int64_t *off2;     // kLearnedBuckets2 + 1 starts of the sub-buckets (the final sort's segments)
+    int64_t *cbase;    // kLearnedBuckets + 1: first second-level chunk of each bucket, then the total
+    int64_t *cnt2;     // chunks x 256 sub-bucket counts, then cursors
 };
 enum LearnedOp { kOpSketch = 0, kOpBucket = 1, kOpSortLearned = 2 };
 struct LearnedCall {
@@ -157,6 +166,8 @@ struct LearnedCall {
     const void *user_spl;    // kOpBucket: caller's splitters (raw keys)
     int nsplit;              // kOpBucket: number of caller's splitters (<= 255)
     int ctas;                // CTAs of the bucket kernels
+    int levels;              // kOpSortLearned: 1 or 2 bucket levels
+    int ctas2;               // CTAs of the second-level passes (an upper bound on the chunks)
     int64_t bound;           // bucket size counted as "over"
     float *sketch_out;       // kOpSketch outputs (device)
     double *minmax_out;

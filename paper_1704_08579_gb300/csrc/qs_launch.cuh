@@ -103,11 +103,25 @@ struct Launcher {
         bucket_scan_kernel<<<1, 1024, 0, s>>>(lb.cnt, lc.ctas, lb.st, nsplit, a.n, lc.bound);
         bucket_scatter_kernel<Tr><<<lc.ctas, kThreads, 0, s>>>(a, lb, nsplit);
         if (lc.op == kOpBucket) return static_cast<int>(cudaGetLastError());
-        // Every bucket is then sorted by the plain method, straight from scratch.
         Args<K, V> a2 = a;
-        a2.seg_off = lb.st->bucket_off;
-        a2.nseg = kBuckets;
-        a2.seg_src = 1;
+        if (lc.levels == 2) {
+            // Second level: every bucket split 256 ways by its own sampled
+            // splitters, from scratch back into the caller's array; then the
+            // 65,536 sub-buckets are sorted by the plain method.
+            sub_splitter_kernel<K><<<kBuckets, 256, 0, s>>>(a.keys[1], lb);
+            chunk_plan_kernel<K><<<1, kBuckets, 0, s>>>(lb);
+            bucket2_hist_kernel<Tr><<<lc.ctas2, kThreads, 0, s>>>(a.keys[1], lb);
+            bucket2_scan_kernel<K><<<kBuckets, 1024, 0, s>>>(lb, a.n);
+            bucket2_scatter_kernel<Tr><<<lc.ctas2, kThreads, 0, s>>>(a, lb);
+            a2.seg_off = lb.off2;
+            a2.nseg = kLearnedBuckets2;
+            a2.seg_src = 0;
+        } else {
+            // Every bucket is sorted by the plain method, straight from scratch.
+            a2.seg_off = lb.st->bucket_off;
+            a2.nseg = kBuckets;
+            a2.seg_src = 1;
+        }
         return launch(a2, cfg);
     }
 };

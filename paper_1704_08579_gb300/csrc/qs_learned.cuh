@@ -33,6 +33,10 @@ struct LearnedBufs {
     typename KeyOps<K>::S *splitters;      // 255 (sort space)
     int64_t *cnt;                          // kBuckets x ctas (bucket-major)
     float *act;                            // MLP activations of one sample
+    typename KeyOps<K>::S *spl2;           // second level: 256 x 256 (each bucket's 255 sorted splitters)
+    int64_t *off2;                         // kLearnedBuckets2 + 1 sub-bucket starts
+    int64_t *cbase;                        // kBuckets + 1 first chunk of each bucket, then the total
+    int64_t *cnt2;                         // per bucket j: 256 x chunks_j counts (sub-bucket-major)
 };
 
 template <class K>
@@ -45,6 +49,10 @@ LearnedBufs<K> bufs_of(const LearnedPtrs &p)
     b.splitters = static_cast<typename KeyOps<K>::S *>(p.splitters);
     b.cnt = p.cnt;
     b.act = p.act;
+    b.spl2 = static_cast<typename KeyOps<K>::S *>(p.spl2);
+    b.off2 = p.off2;
+    b.cbase = p.cbase;
+    b.cnt2 = p.cnt2;
     return b;
 }
 
@@ -208,18 +216,18 @@ struct BucketSmem {
     int hist[kWarps][kBuckets];
 };
 
-// Loads the splitters into shared memory, padding the unused slots with the
-// largest key.  Only a key equal to the largest key can count a pad; such a
-// key belongs to the last bucket anyway, so callers clamp the bucket to nsplit.
-template <class Tr>
-__device__ __forceinline__ void load_splitters(typename KeyOps<typename Tr::K>::S *tree, const LearnedBufs<typename Tr::K> &lb,
-                                               int nsplit)
+// Loads `nsplit` sorted splitters into shared memory as the search tree,
+// padding the unused slots with the largest key.  Only a key equal to the
+// largest key can count a pad; such a key belongs to the last bucket anyway,
+// so callers clamp the bucket to nsplit.
+template <class K>
+__device__ __forceinline__ void load_tree(typename KeyOps<K>::S *tree, const typename KeyOps<K>::S *sorted, int nsplit)
 {
-    using Ops = KeyOps<typename Tr::K>;
+    using Ops = KeyOps<K>;
     for (int i = threadIdx.x + 1; i < 256; i += kThreads) {
         const int k = 31 - __clz(i);  // depth - 1
         const int r = (2 * (i - (1 << k)) + 1) * (1 << (7 - k)) - 1;  // sorted index
-        tree[i] = r < nsplit ? lb.splitters[r] : Ops::s_largest();
+        tree[i] = r < nsplit ? sorted[r] : Ops::s_largest();
     }
 }
 
@@ -243,19 +251,17 @@ __device__ __forceinline__ void prefetch_tiles_l2(const T *p, int64_t from, int6
     }
 }
 
+// Histogram of keys [lo, hi) over the tree in sm.spl (loaded by the caller,
+// followed by a barrier): the count of bucket b goes to cnt[b * stride].
 template <class Tr>
-__global__ void __launch_bounds__(kThreads) bucket_hist_kernel(const typename Tr::K *__restrict__ keys, int64_t n,
-                                                               LearnedBufs<typename Tr::K> lb, int nsplit)
+__device__ __forceinline__ void hist_range(const typename Tr::K *__restrict__ keys, int64_t lo, int64_t hi,
+                                           BucketSmem<Tr> &sm, int nsplit, int64_t *cnt, int64_t stride)
 {
     using Ops = KeyOps<typename Tr::K>;
     constexpr int E = bucket_e<typename Tr::K>(), TILE = kThreads * E;
-    __shared__ BucketSmem<Tr> sm;
     const int tid = threadIdx.x, warp = tid >> 5;
-    load_splitters<Tr>(sm.spl, lb, nsplit);
     for (int i = tid; i < kWarps * kBuckets; i += kThreads) (&sm.hist[0][0])[i] = 0;
     __syncthreads();
-    const int64_t c = blockIdx.x, g = gridDim.x;
-    const int64_t lo = c * n / g, hi = (c + 1) * n / g;
     for (int64_t base = lo; base < hi; base += TILE) {
         // Keep two tiles ahead in L2 (the first tile also covers itself).
         if (base == lo)
@@ -284,16 +290,28 @@ __global__ void __launch_bounds__(kThreads) bucket_hist_kernel(const typename Tr
     for (int bb = tid; bb < kBuckets; bb += kThreads) {
         int sum = 0;
         for (int w = 0; w < kWarps; ++w) sum += sm.hist[w][bb];
-        lb.cnt[static_cast<int64_t>(bb) * g + c] = sum;
+        cnt[static_cast<int64_t>(bb) * stride] = sum;
     }
 }
 
-// One CTA: exclusive scan over (bucket, cta) counts in bucket-major order.
+// First level: CTA c of g takes keys [c*n/g, (c+1)*n/g).
+template <class Tr>
+__global__ void __launch_bounds__(kThreads) bucket_hist_kernel(const typename Tr::K *__restrict__ keys, int64_t n,
+                                                               LearnedBufs<typename Tr::K> lb, int nsplit)
+{
+    __shared__ BucketSmem<Tr> sm;
+    load_tree<typename Tr::K>(sm.spl, lb.splitters, nsplit);
+    const int64_t c = blockIdx.x, g = gridDim.x;
+    hist_range<Tr>(keys, c * n / g, (c + 1) * n / g, sm, nsplit, lb.cnt + c, g);
+}
+
+// Exclusive scan over (bucket, cta) counts in bucket-major order, by one CTA
+// of 1024 threads: every count becomes the first slot of its (bucket, CTA)
+// run, base + all counts before it, and starts[b] = bucket b's first slot.
 // Warp w owns the rows (buckets) w, w+32, ...; lane l a contiguous chunk of
 // ceil(ctas/32) counts of a row.  Row totals are scanned once across the CTA,
-// then every count is replaced by its exclusive prefix.
-static __global__ void __launch_bounds__(1024) bucket_scan_kernel(int64_t *__restrict__ cnt, int ctas, LearnedState *st,
-                                                           int nsplit, int64_t n, int64_t bound)
+// then every count is replaced by its prefix.
+__device__ __forceinline__ void scan_rows(int64_t *__restrict__ cnt, int ctas, long long base, int64_t *starts)
 {
     __shared__ long long tot[kBuckets];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -320,7 +338,7 @@ static __global__ void __launch_bounds__(1024) bucket_scan_kernel(int64_t *__res
             const long long x = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += x;
         }
-        long long run = incl - sum;
+        long long run = base + incl - sum;
 #pragma unroll
         for (int i = 0; i < kBuckets / 32; ++i) {
             tot[lane * (kBuckets / 32) + i] = run;
@@ -344,8 +362,17 @@ static __global__ void __launch_bounds__(1024) bucket_scan_kernel(int64_t *__res
             row[j] = run;
             run += v;
         }
-        if (lane == 0) st->bucket_off[b] = tot[b];
+        if (lane == 0) starts[b] = tot[b];
     }
+}
+
+// First level: one CTA scans the (bucket, CTA) counts, records the bucket
+// starts and the bucket statistics.
+static __global__ void __launch_bounds__(1024) bucket_scan_kernel(int64_t *__restrict__ cnt, int ctas, LearnedState *st,
+                                                           int nsplit, int64_t n, int64_t bound)
+{
+    const int t = threadIdx.x;
+    scan_rows(cnt, ctas, 0, st->bucket_off);
     if (t == 0) st->bucket_off[nsplit + 1] = n;
     __syncthreads();
     // Bucket statistics, one thread per bucket, reduced over the CTA.
@@ -398,32 +425,29 @@ struct ScatterSmem {
     int wsum[kWarps];
 };
 
-// Scatter: each tile's keys are ranked inside their buckets with one shared
-// atomic per key, staged in bucket order, and leave the CTA as one
-// contiguous run per (tile, bucket).  The order of keys inside a bucket is
-// not kept (the buckets are sorted afterwards).
+// Scatter of keys [lo, hi) from sk/sv to dk/dv: each tile's keys are ranked
+// inside their buckets with one shared atomic per key, staged in bucket
+// order, and leave the CTA as one contiguous run per (tile, bucket).  The
+// tree is in sm.spl (loaded by the caller); bucket b's first slot for this
+// CTA is cursor[b * stride] (from the scan); every slot must lie in
+// [0, bound).  The order of keys inside a bucket is not kept (the buckets
+// are sorted afterwards).
 template <class Tr>
-__global__ void __launch_bounds__(kThreads) bucket_scatter_kernel(Args<typename Tr::K, typename Tr::V> a,
-                                                                  LearnedBufs<typename Tr::K> lb, int nsplit)
+__device__ __forceinline__ void scatter_range(const typename Tr::K *__restrict__ sk, const typename Tr::V *__restrict__ sv,
+                                              typename Tr::K *__restrict__ dk, typename Tr::V *__restrict__ dv,
+                                              int64_t lo, int64_t hi, ScatterSmem<Tr> &sm, int nsplit,
+                                              const int64_t *cursor, int64_t stride, int64_t bound, LearnedState *st)
 {
     using K = typename Tr::K;
     using V = typename Tr::V;
     using Ops = KeyOps<K>;
     constexpr int E = bucket_e<K>(), TILE = kThreads * E;
-    __shared__ ScatterSmem<Tr> sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t c = blockIdx.x, g = gridDim.x, n = a.n;
-    const int64_t lo = c * n / g, hi = (c + 1) * n / g;
-    load_splitters<Tr>(sm.spl, lb, nsplit);
     for (int bb = tid; bb < kBuckets; bb += kThreads) {
-        sm.cursor[bb] = lb.cnt[static_cast<int64_t>(bb) * g + c];
+        sm.cursor[bb] = cursor[static_cast<int64_t>(bb) * stride];
         sm.tcnt[bb] = 0;
     }
     __syncthreads();
-    const K *__restrict__ sk = a.keys[0];
-    const V *__restrict__ sv = a.vals[0];
-    K *__restrict__ dk = a.keys[1];
-    V *__restrict__ dv = a.vals[1];
     for (int64_t base = lo; base < hi; base += TILE) {
         // Keep two tiles ahead in L2 (the first tile also covers itself).
         const int64_t pf = base == lo ? base : base + 2 * TILE;
@@ -478,8 +502,8 @@ __global__ void __launch_bounds__(kThreads) bucket_scatter_kernel(Args<typename 
             if (s >= cnt) continue;
             const int bb = sm.bkt[s];
             const long long d = sm.cursor[bb] + (s - sm.tstart[bb]);
-            if (d < 0 || d >= n) {
-                lb.st->status = -7;
+            if (d < 0 || d >= bound) {
+                st->status = -7;
                 continue;
             }
             dk[d] = sm.keys[s];
@@ -490,6 +514,153 @@ __global__ void __launch_bounds__(kThreads) bucket_scatter_kernel(Args<typename 
         sm.tcnt[tid] = 0;
         __syncthreads();
     }
+}
+
+// First level: CTA c of g scatters keys [c*n/g, (c+1)*n/g) from the caller's
+// array into scratch.
+template <class Tr>
+__global__ void __launch_bounds__(kThreads) bucket_scatter_kernel(Args<typename Tr::K, typename Tr::V> a,
+                                                                  LearnedBufs<typename Tr::K> lb, int nsplit)
+{
+    __shared__ ScatterSmem<Tr> sm;
+    load_tree<typename Tr::K>(sm.spl, lb.splitters, nsplit);
+    const int64_t c = blockIdx.x, g = gridDim.x, n = a.n;
+    scatter_range<Tr>(a.keys[0], a.vals[0], a.keys[1], a.vals[1], c * n / g, (c + 1) * n / g, sm, nsplit, lb.cnt + c, g,
+                      n, lb.st);
+}
+
+// ---------------------------------------------------------------------------
+// Second bucket level (sample-sort style): each first-level bucket j, now in
+// scratch at [bucket_off[j], bucket_off[j+1]), is split 256 ways again by its
+// own splitters, from scratch back into the caller's array; the 65,536
+// sub-buckets are then sorted by the plain method (most of them by the leaf
+// kernel alone).  The passes give every CTA one chunk of kBucket2Chunk keys
+// of one bucket, so large and small buckets get CTAs in proportion.
+// ---------------------------------------------------------------------------
+
+// Sub-splitters of bucket j (one CTA of 256 threads per bucket): 1024 keys
+// sampled at jittered strides over the bucket, sorted with the Bitonic group
+// network, every 4th kept -- the sampled form's rule, inside the bucket.
+template <class K>
+__global__ void __launch_bounds__(256) sub_splitter_kernel(const K *__restrict__ keys, LearnedBufs<K> lb)
+{
+    using Ops = KeyOps<K>;
+    using S = typename Ops::S;
+    constexpr int E = sizeof(S) == 8 ? 16 : 32, LE = sizeof(S) == 8 ? 4 : 5;
+    constexpr int NG = kSketchN / E;  // threads of the sorting group
+    __shared__ S sm[kSketchN + kSketchN / 16];
+    const int t = threadIdx.x, j = blockIdx.x;
+    const int64_t lo = lb.st->bucket_off[j], len = lb.st->bucket_off[j + 1] - lo;
+    if (len <= 0) return;  // CTA-uniform: an empty bucket has no chunks either
+    const int64_t stride = len / kSketchN;
+    for (int i = t; i < kSketchN; i += 256) {
+        const uint64_t h = mix64(static_cast<uint64_t>(lo) * 0x9E3779B97F4A7C15ull + i);
+        const int64_t pos = (static_cast<int64_t>(i) * len) / kSketchN +
+                            static_cast<int64_t>(h % static_cast<uint64_t>(stride > 0 ? stride : 1));
+        sm[padk<S>(i)] = Ops::to_s(keys[lo + (pos < len ? pos : len - 1)]);
+    }
+    __syncthreads();
+    if (t < NG) {
+        S k[E];
+        lay_load<E, LE, S>(k, sm, t, 0);
+        group_bitonic_sort<E, LE, 10, S>(k, sm, t, 1, NG);
+        group_sync(1, NG);
+        lay_store<E, LE, S>(k, sm, t, 0);
+    }
+    __syncthreads();
+    if (t < kBuckets - 1) lb.spl2[static_cast<int64_t>(j) * kBuckets + t] = sm[padk<S>(4 * (t + 1))];
+}
+
+// One CTA of kBuckets threads: chunks per bucket, their exclusive prefix
+// (cbase[j] = the first chunk of bucket j, cbase[kBuckets] = all chunks).
+template <class K>
+__global__ void __launch_bounds__(kBuckets) chunk_plan_kernel(LearnedBufs<K> lb)
+{
+    __shared__ long long wsum[kBuckets / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t len = lb.st->bucket_off[t + 1] - lb.st->bucket_off[t];
+    const long long v = len > 0 ? (len + kBucket2Chunk - 1) / kBucket2Chunk : 0;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long x = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += x;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    long long add = 0;
+    for (int w = 0; w < warp; ++w) add += wsum[w];
+    lb.cbase[t] = add + incl - v;
+    if (t == kBuckets - 1) lb.cbase[kBuckets] = add + incl;
+}
+
+// The chunk of CTA b: bucket j (cbase[j] <= b < cbase[j+1]), its index c in
+// the bucket, the bucket's chunk count, and the key range; false when b lies
+// past the last chunk (the grid is an upper bound).
+template <class K>
+__device__ __forceinline__ bool chunk_of(const LearnedBufs<K> &lb, long long b, int &j, long long &c, long long &nch,
+                                         int64_t &lo, int64_t &hi)
+{
+    if (b >= lb.cbase[kBuckets]) return false;
+    int l = 0, r = kBuckets;  // largest j with cbase[j] <= b
+    while (r - l > 1) {
+        const int m = (l + r) >> 1;
+        if (lb.cbase[m] <= b)
+            l = m;
+        else
+            r = m;
+    }
+    j = l;
+    c = b - lb.cbase[j];
+    nch = lb.cbase[j + 1] - lb.cbase[j];
+    const int64_t start = lb.st->bucket_off[j], end = lb.st->bucket_off[j + 1];
+    lo = start + c * kBucket2Chunk;
+    hi = lo + kBucket2Chunk < end ? lo + kBucket2Chunk : end;
+    return true;
+}
+
+template <class Tr>
+__global__ void __launch_bounds__(kThreads) bucket2_hist_kernel(const typename Tr::K *__restrict__ keys,
+                                                                LearnedBufs<typename Tr::K> lb)
+{
+    __shared__ BucketSmem<Tr> sm;
+    int j;
+    long long c, nch;
+    int64_t lo, hi;
+    if (!chunk_of(lb, blockIdx.x, j, c, nch, lo, hi)) return;  // CTA-uniform
+    load_tree<typename Tr::K>(sm.spl, lb.spl2 + static_cast<int64_t>(j) * kBuckets, kBuckets - 1);
+    hist_range<Tr>(keys, lo, hi, sm, kBuckets - 1, lb.cnt2 + lb.cbase[j] * kBuckets + c, nch);
+}
+
+// One CTA of 1024 threads per bucket j: its (sub-bucket, chunk) counts become
+// cursors, its sub-bucket starts go to off2[j*256 ...]; off2 ends with n.
+template <class K>
+__global__ void __launch_bounds__(1024) bucket2_scan_kernel(LearnedBufs<K> lb, int64_t n)
+{
+    const int j = blockIdx.x, t = threadIdx.x;
+    const long long nch = lb.cbase[j + 1] - lb.cbase[j];
+    const long long base = lb.st->bucket_off[j];
+    int64_t *starts = lb.off2 + static_cast<int64_t>(j) * kBuckets;
+    if (nch == 0) {  // CTA-uniform
+        if (t < kBuckets) starts[t] = base;
+    } else {
+        scan_rows(lb.cnt2 + lb.cbase[j] * kBuckets, static_cast<int>(nch), base, starts);
+    }
+    if (j == 0 && t == 0) lb.off2[kLearnedBuckets2] = n;
+}
+
+template <class Tr>
+__global__ void __launch_bounds__(kThreads) bucket2_scatter_kernel(Args<typename Tr::K, typename Tr::V> a,
+                                                                   LearnedBufs<typename Tr::K> lb)
+{
+    __shared__ ScatterSmem<Tr> sm;
+    int j;
+    long long c, nch;
+    int64_t lo, hi;
+    if (!chunk_of(lb, blockIdx.x, j, c, nch, lo, hi)) return;  // CTA-uniform
+    load_tree<typename Tr::K>(sm.spl, lb.spl2 + static_cast<int64_t>(j) * kBuckets, kBuckets - 1);
+    scatter_range<Tr>(a.keys[1], a.vals[1], a.keys[0], a.vals[0], lo, hi, sm, kBuckets - 1,
+                      lb.cnt2 + lb.cbase[j] * kBuckets + c, nch, a.n, lb.st);
 }
 
 }  // namespace qs

@@ -237,9 +237,19 @@ def _model(which: str, seed: int = 41):
     return torch.from_numpy(p).to("cuda")
 
 
+@pytest.fixture(params=[1, 2], ids=["one_level", "two_levels"])
+def levels(request):
+    """QS_OPT_BUCKET_LEVELS for the test (one 256-way bucket pass, or a
+    second one inside every bucket); restored to the default afterwards."""
+    qs = qs_gpu()
+    qs.set_option("bucket_levels", request.param)
+    yield request.param
+    qs.set_option("bucket_levels", 0)
+
+
 @pytest.mark.parametrize("kind", ["zipf", "gmix", "lognormal"])
 @pytest.mark.parametrize("which", ["sampled", "untrained", "random", "collapse", "front"])
-def test_learned_sort_matches_oracle(kind, which):
+def test_learned_sort_matches_oracle(kind, which, levels):
     qs = qs_gpu()
     n = (1 << 20) + 4321
     x = _keys(kind, n, 2)
@@ -252,8 +262,8 @@ def test_learned_sort_matches_oracle(kind, which):
         assert st["bucket_over"] >= 1, "a degenerate model must trip the size bound"
 
 
-@pytest.mark.parametrize("n", [0, 1, 1000, (1 << 16) - 1, 1 << 16, (1 << 16) + 1, 3 << 18])
-def test_learned_sort_sizes(n):
+@pytest.mark.parametrize("n", [0, 1, 1000, (1 << 16) - 1, 1 << 16, (1 << 16) + 1, 3 << 18, (1 << 22) + 65537])
+def test_learned_sort_sizes(n, levels):
     qs = qs_gpu()
     x = synth.uniform_i32(n, 0x515)
     d = to_dev(x)
@@ -262,7 +272,7 @@ def test_learned_sort_sizes(n):
 
 
 @pytest.mark.parametrize("dtype", ["i32", "f64"])
-def test_learned_sort_degenerate_inputs(dtype):
+def test_learned_sort_degenerate_inputs(dtype, levels):
     """All keys equal, sorted and reverse-sorted input, two distinct keys."""
     qs = qs_gpu()
     n = 300000
@@ -321,3 +331,31 @@ def test_training_gain(kind):
     ml = float(np.mean([d["learned"] for d in cmp.values()]))
     ms = float(np.mean([d["sampled"] for d in cmp.values()]))
     assert ml < ms
+
+
+@pytest.mark.parametrize("dtype", ["i32", "f64"])
+def test_two_level_buckets_skewed_and_chunked(dtype):
+    """Second bucket level: buckets of very different sizes (Zipf / lognormal
+    keys, so some buckets span many chunks of the second-level passes and
+    others are empty), a heavy key that fills whole sub-buckets, and sizes
+    that leave a ragged last chunk -- against the oracle."""
+    qs = qs_gpu()
+    try:
+        qs.set_option("bucket_levels", 2)
+        for n in ((1 << 21) + 12345, (1 << 23) + 3):
+            if dtype == "i32":
+                x = synth.zipf_i32(n, 17)
+            else:
+                x = synth.lognormal_f64(n, 18)
+            for which in ("sampled", "random"):
+                d = to_dev(x)
+                qs.sort_learned(d, _model(which))
+                assert_keys_equal(d.cpu().numpy(), oracle.sort(x))
+        heavy = np.where(synth.mod_i32(1 << 20, 19, 3) == 0, 5, synth.uniform_i32(1 << 20, 20)).astype(np.int32)
+        if dtype == "f64":
+            heavy = heavy.astype(np.float64) * 0.5
+        d = to_dev(heavy)
+        qs.sort_learned(d, _model("sampled"))
+        assert_keys_equal(d.cpu().numpy(), oracle.sort(heavy))
+    finally:
+        qs.set_option("bucket_levels", 0)
