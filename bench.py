@@ -469,8 +469,9 @@ def _learned(torch, qs, stream, steps=3):
     over 2^24 values, 2^30 int32 keys from an 8-Gaussian mixture, 2^28 FP64
     keys lognormal(0, 2).  The network is first trained (untimed) on
     sort-generated pairs with the library's kernels; then the plain sort, the
-    bucket form with sampled splitters and the learned form are timed on the
-    same array (median of `steps`), and the bucket forms' outputs are checked
+    bucket form with sampled splitters and the learned form (two bucket
+    levels, the default; and again with one level) are timed on the same
+    array (median of `steps`), and the bucket forms' outputs are checked
     equal to the plain sort's."""
     import synth.device as sdev
     from paper_1704_08579_gb300 import learned
@@ -493,7 +494,8 @@ def _learned(torch, qs, stream, steps=3):
         work = torch.empty_like(pristine)
         ref = None
         res = {}
-        for arm in ("plain", "sampled", "learned"):
+        for arm in ("plain", "sampled", "learned", "sampled_1level", "learned_1level"):
+            qs.set_option("bucket_levels", 1 if arm.endswith("_1level") else 0)
             times, st = [], None
             for r in range(steps + 1):
                 work.copy_(pristine)
@@ -505,7 +507,7 @@ def _learned(torch, qs, stream, steps=3):
                     if arm == "plain":
                         qs.sort(work, stream=stream)
                     else:
-                        qs.sort_learned(work, models[kind] if arm == "learned" else None, stream=stream)
+                        qs.sort_learned(work, models[kind] if arm.startswith("learned") else None, stream=stream)
                     b.record(stream)
                 b.synchronize()
                 st = qs.stats()
@@ -522,7 +524,9 @@ def _learned(torch, qs, stream, steps=3):
                                  "buckets_over_bound": st["bucket_over"],
                                  "equal_to_plain": bool(torch.equal(work.view(torch.int64) if kind == "f64" else work,
                                                                     ref.view(torch.int64) if kind == "f64" else ref))})
+        qs.set_option("bucket_levels", 0)
         res["n"] = n
+        res["bucket_levels"] = {"sampled": 2, "learned": 2, "sampled_1level": 1, "learned_1level": 1}
         out[name] = res
         del pristine, work, ref
         torch.cuda.empty_cache()
