@@ -351,16 +351,18 @@ int qs_get_stats(qs_stats *out);
  *                        GB300 for uniform keys, hence not the default).
  *   QS_OPT_SMALL_MAX     parts of at most this many keys (power of two, >= 32)
  *                        are sorted by one warp; 0 = the compiled maximum 512.
- *   QS_OPT_DRIVER_ITEMS  keys per thread of a partition tile: each kind has a
- *                        wide and a narrow compiled variant (i32 32 / 16,
- *                        f64 16 / 8, kv 16 / 8), and f64 and kv a register
- *                        tile of 32 keys per thread (64 KB, loaded straight
- *                        into registers, no prefetch buffer, 2 CTAs per SM);
- *                        the narrow or register-tile value selects that
- *                        variant, any other non-zero value the wide one, 0
- *                        the kind's default: for sorts i32 wide, f64 and kv
- *                        the register tile; for partitions i32 narrow, f64
- *                        and kv wide.
+ *   QS_OPT_DRIVER_ITEMS  keys per thread of a partition tile: f64 and kv have
+ *                        a wide and a narrow prefetched variant (16 / 8;
+ *                        the next tile brought into shared memory by a TMA
+ *                        copy) and a register tile of 32 keys per thread
+ *                        (64 KB, loaded straight into registers, no prefetch
+ *                        buffer, 2 CTAs per SM); i32 has a register tile of
+ *                        32 keys per thread (32 KB, 4 CTAs per SM) and a
+ *                        narrow prefetched variant of 16; the narrow or
+ *                        register-tile value selects that variant, any other
+ *                        non-zero value the wide one (i32: the register
+ *                        tile), 0 the kind's default: for sorts the register
+ *                        tile; for partitions i32 narrow, f64 and kv wide.
  *   QS_OPT_ORDERED       0 (default): inside a sort, each partition tile
  *                        claims its lower- and upper-side output ranges with
  *                        one atomic add each on its task's two counters, so

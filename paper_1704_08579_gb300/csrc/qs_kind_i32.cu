@@ -5,15 +5,16 @@ namespace qs {
 
 namespace {
 // Two partition tile variants (items per thread), chosen per call by
-// QS_OPT_DRIVER_ITEMS (the autotuner).  Sorts default to the wide one (2^28
-// keys: 8.08 ms of partition passes against 8.39 for the narrow one at 4 CTAs
-// per SM); partitions keep the narrow one.
-using Tr = Traits<int32_t, false, 8, 32768, 512>;
+// QS_OPT_DRIVER_ITEMS (the autotuner): the register tile -- 32 keys per
+// thread, 32 KB loaded straight into registers with 16-byte loads, the next
+// tile prefetched into L2, 4 CTAs per SM (64 registers) -- the sorts'
+// default (2^28 keys: 7.05 ms of partition passes against 8.30 for the
+// prefetched 32-key tile it replaced), and the narrow prefetched tile (16
+// keys, TMA double buffer, 4 CTAs per SM), the partitions' default.  The
+// leaf kernel runs one 1024-thread CTA per SM.
+using Tr = Traits<int32_t, false, 8, 32768, 512, false>;
 using TrN = Traits<int32_t, false, 4, 32768, 512>;
-// Minimum CTAs per SM of the persistent partition kernel: 3 (80 registers
-// per thread); the narrow int32 tile 4 (64 registers).  The leaf kernel
-// runs one 1024-thread CTA per SM.
-using L = Launcher<Tr, 3 * 256 / kDThreads>;
+using L = Launcher<Tr, 4>;
 using LN = Launcher<TrN, 4>;
 }  // namespace
 
@@ -27,7 +28,7 @@ KernelLimits limits_i32()
     l.tile = TrN::T < Tr::T ? TrN::T : Tr::T;
     l.items_wide = Tr::E;
     l.items_narrow = TrN::E;
-    l.items_xwide = 0;  // a register tile would need 64 keys per thread
+    l.items_xwide = 0;  // the 32-key variant is itself a register tile
     l.items_default = Tr::E;
     l.items_default_part = TrN::E;
     return l;

@@ -80,7 +80,7 @@ extern "C" int64_t qs_partition_i32_noalloc(int32_t *d_keys, int64_t n, int32_t 
             return fail(QS_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
         int sms = 0, bps = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            occupancy_i32(0, &bps) != cudaSuccess || bps < 1)
+            occupancy_i32(2, &bps) != cudaSuccess || bps < 1)  // the partitions' (narrow) tile
             return fail(QS_ERR_CUDA, "device query failed");
         su.base = static_cast<unsigned char *>(p);
         su.grid = sms * bps;
@@ -123,6 +123,7 @@ extern "C" int64_t qs_partition_i32_noalloc(int32_t *d_keys, int64_t n, int32_t 
     cfg.stream = s;
     cfg.grid_driver = su.grid;
     cfg.grid_leaf = su.grid;
+    cfg.items = lim.items_default_part;  // the tile qs_partition_i32 uses
     cfg.profile = 0;
     if (launch_i32(a, cfg) != cudaSuccess) return fail(QS_ERR_CUDA, "kernel launch failed");
     Ctrl h;  // pageable host copy of the control block: no host allocation either
