@@ -109,7 +109,8 @@ __device__ __forceinline__ bool goes_low(typename Ops::Raw k, typename Ops::Raw 
 //         buffer by a TMA bulk copy; false: a tile is loaded straight into
 //         registers with 16-byte loads (one shared-memory buffer, for
 //         staging only), for tiles too large to double-buffer
-template <class K_, bool KV_, int VPT_, int LEAF_, int SMALL_, bool PF_ = true>
+//   DT    threads per CTA of the persistent partition kernel
+template <class K_, bool KV_, int VPT_, int LEAF_, int SMALL_, bool PF_ = true, int DT_ = kDThreads>
 struct Traits {
     using K = K_;
     using V = int32_t;
@@ -118,13 +119,16 @@ struct Traits {
     static constexpr int VW = KeyOps<K>::VW;
     static constexpr int VPT = VPT_;
     static constexpr int E = VPT_ * KeyOps<K_>::VW;  // keys per thread per tile
-    static constexpr int T = kDThreads * E;  // keys per partition tile
+    static constexpr int DT = DT_;
+    static constexpr int DW = DT_ / 32;
+    static constexpr int T = DT_ * E;  // keys per partition tile
     static constexpr int LEAF = LEAF_;
     static constexpr int MID = 2 * LEAF_;
     static constexpr int SMALL = SMALL_;
     static constexpr bool PF = PF_;
     static constexpr int NBUF = PF_ ? 2 : 1;  // shared-memory tile buffers
     static_assert(E <= 32, "per-thread flags are kept in one 32-bit mask");
+    static_assert(DT_ % 32 == 0 && DT_ >= 128 && DT_ <= 1024, "whole warps; warp 0, the middle warps and the last warp");
 };
 
 // ---------------------------------------------------------------------------

@@ -222,15 +222,13 @@ struct WorkItem {
     uint64_t pivot;
 };
 
-// Warps 1 .. kDWarps-2 count the prefetched tile during the look-back.
-constexpr int kCountThreads = kDThreads - 64;
 
 template <class Tr>
 struct DriverSmem {
     alignas(128) typename Tr::K kbuf[Tr::NBUF][Tr::T];
     alignas(128) typename Tr::V vbuf[Tr::NBUF][Tr::KV ? Tr::T : 4];
     alignas(8) unsigned long long bar[2];
-    int wcount[Tr::VPT * kDWarps];
+    int wcount[Tr::VPT * Tr::DW];
     long long excl;
     long long hexcl;  // unordered placement: upper-side keys placed before this tile
     long long first;
@@ -440,6 +438,8 @@ __device__ __forceinline__ uint32_t low_mask(const typename Tr::K (&key)[Tr::E],
     return m & validm;
 }
 
+// Lower-side count of a prefetched tile in shared memory, by the middle warps
+// (1 .. DW-2) during the look-back.
 template <class Tr, bool LE, bool NEG>
 __device__ __forceinline__ int count_low(const typename Tr::K *buf, typename KeyOps<typename Tr::K>::Raw p)
 {
@@ -448,7 +448,7 @@ __device__ __forceinline__ int count_low(const typename Tr::K *buf, typename Key
     constexpr int NV = Tr::T / Tr::VW;
     const Vec *v = reinterpret_cast<const Vec *>(buf);
     int cnt = 0;
-    for (int i = threadIdx.x - 32; i < NV; i += kCountThreads) {
+    for (int i = threadIdx.x - 32; i < NV; i += Tr::DT - 64) {
         typename Tr::K tmp[Tr::VW];
         Ops::split(v[i], tmp);
 #pragma unroll
@@ -542,7 +542,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     using Ops = KeyOps<K>;
     using Vec = typename Ops::Vec;
     constexpr int VW = Tr::VW, VPT = Tr::VPT, T = Tr::T, E = Tr::E;
-    constexpr int NC = VPT * kDWarps;       // (vector, warp) chunk counts
+    constexpr int NC = VPT * Tr::DW;       // (vector, warp) chunk counts
     constexpr int CPL = (NC + 31) / 32;    // chunk counts per lane in the scan
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -562,7 +562,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     // its fence waits for this SM's earlier stores to drain while the other
     // warps compare.  (Ordered placement releases in the look-back phase,
     // where the middle warps count the next tile meanwhile.)
-    if (!a.ordered && warp == kDWarps - 1) {
+    if (!a.ordered && warp == Tr::DW - 1) {
         if (lane == 0) {
             const long long trl = a.profile ? prof_clock() : 0;
             release_prev<Tr>(a, sm);
@@ -590,11 +590,11 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
             K tmp[VW];
-            Ops::split(__ldcg(gk + k * kDThreads + tid), tmp);
+            Ops::split(__ldcg(gk + k * Tr::DT + tid), tmp);
 #pragma unroll
             for (int j = 0; j < VW; ++j) key[k * VW + j] = tmp[j];
             if constexpr (Tr::KV) {
-                const int4 vv = __ldcg(gv + k * kDThreads + tid);
+                const int4 vv = __ldcg(gv + k * Tr::DT + tid);
                 val[k * VW + 0] = vv.x;
                 val[k * VW + 1] = vv.y;
                 val[k * VW + 2] = vv.z;
@@ -611,7 +611,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         for (int k = 0; k < VPT; ++k) {
             K tmp[VW];
             if (landed) {
-                Ops::split(sv[k * kDThreads + tid], tmp);
+                Ops::split(sv[k * Tr::DT + tid], tmp);
             } else {
 #pragma unroll
                 for (int j = 0; j < VW; ++j) tmp[j] = K(0);
@@ -619,7 +619,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
 #pragma unroll
             for (int j = 0; j < VW; ++j) key[k * VW + j] = tmp[j];
             if constexpr (Tr::KV) {
-                const int4 vv = landed ? reinterpret_cast<const int4 *>(sm.vbuf[b])[k * kDThreads + tid]
+                const int4 vv = landed ? reinterpret_cast<const int4 *>(sm.vbuf[b])[k * Tr::DT + tid]
                                        : make_int4(0, 0, 0, 0);
                 val[k * VW + 0] = vv.x;
                 val[k * VW + 1] = vv.y;
@@ -633,7 +633,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         const V *__restrict__ svv = a.vals[w.src];
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
-            const int64_t e = base + static_cast<int64_t>(k) * kDThreads * VW + tid * VW;
+            const int64_t e = base + static_cast<int64_t>(k) * Tr::DT * VW + tid * VW;
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
                 const int64_t p = e + j;
@@ -659,7 +659,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
             pre += __popc(bb & lt_mask);
         }
         rank[k] = pre;
-        if (lane == 0) sm.wcount[k * kDWarps + warp] = tot;
+        if (lane == 0) sm.wcount[k * Tr::DW + warp] = tot;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) eq += __shfl_xor_sync(0xffffffffu, eq, o);
@@ -676,12 +676,12 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
             const char *kb = reinterpret_cast<const char *>(a.keys[nx.src] + nbase);
             constexpr int kLines = T * static_cast<int>(sizeof(K)) / 128;
 #pragma unroll
-            for (int q = tid; q < kLines; q += kDThreads) asm volatile("prefetch.global.L2 [%0];" ::"l"(kb + q * 128));
+            for (int q = tid; q < kLines; q += Tr::DT) asm volatile("prefetch.global.L2 [%0];" ::"l"(kb + q * 128));
             if constexpr (Tr::KV) {
                 const char *vb = reinterpret_cast<const char *>(a.vals[nx.src] + nbase);
                 constexpr int vLines = T * static_cast<int>(sizeof(V)) / 128;
 #pragma unroll
-                for (int q = tid; q < vLines; q += kDThreads)
+                for (int q = tid; q < vLines; q += Tr::DT)
                     asm volatile("prefetch.global.L2 [%0];" ::"l"(vb + q * 128));
             }
         }
@@ -703,8 +703,8 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
     auto stage = [&](int L) {
 #pragma unroll
         for (int k = 0; k < VPT; ++k) {
-            int r = sm.wcount[k * kDWarps + warp] + rank[k];
-            const int e = k * kDThreads * VW + tid * VW - vofs;
+            int r = sm.wcount[k * Tr::DW + warp] + rank[k];
+            const int e = k * Tr::DT * VW + tid * VW - vofs;
 #pragma unroll
             for (int j = 0; j < VW; ++j) {
                 const int i = k * VW + j;
@@ -743,7 +743,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         }
         if (lane == 0) sm.low_total = total;
         __syncwarp();
-        asm volatile("bar.arrive 2, %0;" ::"n"(kDThreads) : "memory");
+        asm volatile("bar.arrive 2, %0;" ::"n"(Tr::DT) : "memory");
         const long long tlb = a.profile ? prof_clock() : 0;
         if (a.ordered) {
             int nwin, nspin;
@@ -794,7 +794,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
                 sm.tm[14] += now - tph;
             }
         }
-    } else if (warp < kDWarps - 1) {
+    } else if (warp < Tr::DW - 1) {
         if (Tr::PF && a.ordered && nx.kind == 1 && nx.full && !nx.a_pub) {
             // The middle warps first count the prefetched next tile and
             // publish its aggregate, so tiles after it never wait for this CTA
@@ -808,7 +808,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
                 for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
                 if (lane == 0) atomicAdd(&sm.next_low, cnt);
             }
-            asm volatile("bar.sync 1, %0;" ::"n"(kCountThreads) : "memory");
+            asm volatile("bar.sync 1, %0;" ::"n"(Tr::DT - 64) : "memory");
             if (tid == 32) {
                 const unsigned long long c = static_cast<unsigned long long>(sm.next_low);
                 st_relaxed_u64(a.pool + nx.pool + nx.tile, (nx.tile == 0 ? kFlagPrefix : kFlagAggregate) | c);
@@ -816,7 +816,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
                 nx.a_pub = 1;
             }
         }
-        asm volatile("bar.sync 2, %0;" ::"n"(kDThreads) : "memory");  // chunk offsets are ready
+        asm volatile("bar.sync 2, %0;" ::"n"(Tr::DT) : "memory");  // chunk offsets are ready
         stage(sm.low_total);
         if (a.profile && tid == 32) sm.tm[12] += prof_clock() - tph;
     } else {
@@ -828,7 +828,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
             }
             __syncwarp();
         }
-        asm volatile("bar.sync 2, %0;" ::"n"(kDThreads) : "memory");  // chunk offsets are ready
+        asm volatile("bar.sync 2, %0;" ::"n"(Tr::DT) : "memory");  // chunk offsets are ready
         const long long tst = a.profile ? prof_clock() : 0;
         stage(sm.low_total);
         if (a.profile && lane == 0) {
@@ -860,7 +860,7 @@ __device__ int partition_tile(const Args<typename Tr::K, typename Tr::V> &a, con
         K *__restrict__ hi_k = a.keys[w.src ^ 1] + (end - 1 - hpre + L);  // key s >= L goes to hi_k - s
         V *__restrict__ lo_v = a.vals[lo_buf] + (off + excl);
         V *__restrict__ hi_v = a.vals[w.src ^ 1] + (end - 1 - hpre + L);
-        for (int s = tid; s < nvalid; s += kDThreads) {
+        for (int s = tid; s < nvalid; s += Tr::DT) {
             const bool lo = s < L;
             *(lo ? lo_k + s : hi_k - s) = stage_k[s];
             if constexpr (Tr::KV) *(lo ? lo_v + s : hi_v - s) = stage_v[s];
@@ -985,7 +985,7 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
     }
     __syncthreads();
     for (int i = 0; i < 2; ++i)
-        if (sm.nt_ok[i]) publish_task(a.owner, sm.nt[i], -1, kDThreads);
+        if (sm.nt_ok[i]) publish_task(a.owner, sm.nt[i], -1, Tr::DT);
     if (a.profile && tid == 0) sm.tm[28] += prof_clock() - tf;
     for (int i = 0; i < 2; ++i) {
         // Finished run of equal keys: copy back if it sits in scratch, or
@@ -1002,7 +1002,7 @@ __device__ void finish_task(const Args<typename Tr::K, typename Tr::V> &a, const
         __syncthreads();
         const long long first = sm.first;
         if (first >= 0) {
-            for (int64_t q = tid; q < chunks; q += kDThreads) {
+            for (int64_t q = tid; q < chunks; q += Tr::DT) {
                 Leaf l;
                 l.off = coff + q * kCopyChunk;
                 const int64_t rem = clen - q * kCopyChunk;
@@ -1040,7 +1040,7 @@ __device__ void flush_release(const Args<typename Tr::K, typename Tr::V> &a, Dri
 // Persistent partition kernel.
 // ---------------------------------------------------------------------------
 template <class Tr, int MinBlocks>
-__global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typename Tr::K, typename Tr::V> a)
+__global__ void __launch_bounds__(Tr::DT, MinBlocks) driver_kernel(Args<typename Tr::K, typename Tr::V> a)
 {
     extern __shared__ __align__(128) unsigned char dyn_smem[];
     DriverSmem<Tr> &sm = *reinterpret_cast<DriverSmem<Tr> *>(dyn_smem);
@@ -1150,8 +1150,8 @@ __global__ void __launch_bounds__(kDThreads, MinBlocks) driver_kernel(Args<typen
     // look-back words; the host clears the words it used before the next call.)
     if (!a.partition_only && ld_relaxed_s32(&a.ctrl->status) == 0) {
         const unsigned long long used = ld_relaxed_u64(&a.ctrl->pool_cursor);
-        const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * kDThreads;
-        for (unsigned long long i = blockIdx.x * kDThreads + tid; i < used; i += stride) {
+        const unsigned long long stride = static_cast<unsigned long long>(gridDim.x) * Tr::DT;
+        for (unsigned long long i = blockIdx.x * Tr::DT + tid; i < used; i += stride) {
             a.pool[i] = 0;
             a.owner[i] = 0;
         }

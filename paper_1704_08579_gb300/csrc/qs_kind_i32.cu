@@ -9,7 +9,8 @@ namespace {
 // thread, 32 KB loaded straight into registers with 16-byte loads, the next
 // tile prefetched into L2, 4 CTAs per SM (64 registers) -- the sorts'
 // default (2^28 keys: 7.05 ms of partition passes against 8.30 for the
-// prefetched 32-key tile it replaced), and the narrow prefetched tile (16
+// prefetched 32-key tile it replaced; the same tile on 512-thread CTAs, 64
+// KB at 2 CTAs per SM: 7.69 ms), and the narrow prefetched tile (16
 // keys, TMA double buffer, 4 CTAs per SM), the partitions' default.  The
 // leaf kernel runs one 1024-thread CTA per SM.
 using Tr = Traits<int32_t, false, 8, 32768, 512, false>;

@@ -52,7 +52,7 @@ struct Launcher {
         int rc = prepare();
         if (rc) return rc;
         if (which == 0)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, driver_kernel<Tr, DriverMin>, kDThreads,
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, driver_kernel<Tr, DriverMin>, Tr::DT,
                                                                  kDriverSmem);
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, leaf_kernel<LTr, false>, kLThreads,
                                                              LeafCfg<LTr>::kDynSmem);
@@ -71,7 +71,7 @@ struct Launcher {
         }
         if (cfg.profile) cudaEventRecord(ev[1], s);
         if (a.partition_only || a.seg_off || a.n > a.leaf_max)
-            driver_kernel<Tr, DriverMin><<<cfg.grid_driver, kDThreads, kDriverSmem, s>>>(a);
+            driver_kernel<Tr, DriverMin><<<cfg.grid_driver, Tr::DT, kDriverSmem, s>>>(a);
         if (cfg.profile) cudaEventRecord(ev[2], s);
         if (!a.partition_only) {
             // Parts above LEAF are listed only when the threshold allows them.
