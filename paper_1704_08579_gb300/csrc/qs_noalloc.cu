@@ -41,7 +41,7 @@ constexpr size_t kBytes = align_up(kOffCtrl + sizeof(Ctrl));
 
 // The scratch.  In host code this name is only a stand-in for the device
 // array: its device address comes from cudaGetSymbolAddress below.
-__device__ __align__(256) unsigned char g_noalloc_scratch[kBytes];
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kBytes];
 
 struct DeviceSetup {
     bool ready = false;
