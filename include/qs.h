@@ -354,9 +354,10 @@ int qs_get_stats(qs_stats *out);
  *   QS_OPT_DRIVER_ITEMS  keys per thread of a partition tile: f64 and kv have
  *                        a wide and a narrow prefetched variant (16 / 8;
  *                        the next tile brought into shared memory by a TMA
- *                        copy) and a register tile of 32 keys per thread
- *                        (64 KB, loaded straight into registers, no prefetch
- *                        buffer, 2 CTAs per SM); i32 has a register tile of
+ *                        copy) and a register tile of 20 keys per thread
+ *                        (128-thread CTAs, 20 KB, loaded straight into
+ *                        registers, no prefetch buffer, 6 CTAs per SM);
+ *                        i32 has a register tile of
  *                        32 keys per thread (32 KB, 4 CTAs per SM) and a
  *                        narrow prefetched variant of 16; the narrow or
  *                        register-tile value selects that variant, any other

@@ -22,7 +22,7 @@ CACHE_DIR = os.path.join(HERE, "tuning")
 # size to the leaf kernel, which then splits them once itself.
 LEAF_CHOICES = {"i32": (8192, 16384, 32768, 65536), "f64": (4096, 8192, 16384, 32768), "kv": (4096, 8192, 16384, 32768)}
 SMALL_CHOICES = (128, 256, 512)
-ITEMS_CHOICES = {"i32": (32, 16), "f64": (32, 16, 8), "kv": (32, 16, 8)}  # the kind's sort default first
+ITEMS_CHOICES = {"i32": (32, 16), "f64": (20, 16, 8), "kv": (20, 16, 8)}  # the kind's sort default first
 
 
 def _cache_path(gpu_name: str) -> str:
