@@ -140,6 +140,37 @@ def _dist_env():
     return rank, world, local
 
 
+def _max_over_ranks(torch, value: float, world: int, device: str = "cuda") -> float:
+    """The largest of every rank's `value` (the job's time is its slowest
+    replica's); `device` is where the collective's tensor lives: "cuda" for
+    NCCL, "cpu" for gloo."""
+    if world <= 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_gkeys_s(world: int, keys_per_rank: int, ms_per_step: float) -> float:
+    """Whole-job throughput: the keys of all replicas over the slowest one's time."""
+    return world * keys_per_rank / (ms_per_step / 1e3) / 1e9
+
+
+def _job_e2e(torch, e2e: dict, world: int, keys_per_rank: int, device: str = "cuda") -> dict:
+    """One replica's end-to-end record turned into the job's: the slowest
+    replica's median step, the keys and copied bytes of all replicas."""
+    if world <= 1:
+        return e2e
+    out = dict(e2e)
+    out["ms_per_step"] = _max_over_ranks(torch, e2e["ms_per_step"], world, device)
+    out["value"] = _job_gkeys_s(world, keys_per_rank, out["ms_per_step"])
+    out["h2d_bytes_per_step"] = e2e["h2d_bytes_per_step"] * world
+    out["d2h_bytes_per_step"] = e2e["d2h_bytes_per_step"] * world
+    out["ms_min"] = out["ms_max"] = None  # per-replica extremes are not aggregated
+    out["sorted"] = _max_over_ranks(torch, 0.0 if e2e["sorted"] else 1.0, world, device) == 0.0
+    return out
+
+
 def _device_id(torch, local_rank):
     try:
         uuid = str(torch.cuda.get_device_properties(local_rank).uuid)
@@ -311,9 +342,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
     if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = _max_over_ranks(torch, ms, world)
         torch.distributed.barrier()
     # sanity: every timed output is sorted (a property check, not parity)
     for b in bufs[args.warmup:args.warmup + 2]:
@@ -326,7 +355,7 @@ def run_ours(args):
     torch.cuda.empty_cache()
 
     ms_step = ms / args.steps
-    value = world * N_KEYS / (ms_step / 1e3) / 1e9
+    value = _job_gkeys_s(world, N_KEYS, ms_step)
     drv_ms = statistics.mean(s["ms_driver"] for s in st)
     leaf_ms = statistics.mean(s["ms_leaf"] for s in st)
     part_keys = statistics.mean(s["part_keys"] for s in st)
@@ -356,8 +385,13 @@ def run_ours(args):
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
+    # End to end on every replica at once (each through its own host link);
+    # the job's step is the slowest replica's median step.
+    if world > 1:
+        torch.distributed.barrier()
+    e2e = _job_e2e(torch, _e2e(torch, qs, host, stream, args), world, N_KEYS)
     if rank == 0:
-        line["e2e"] = _e2e(torch, qs, host, stream, args)
+        line["e2e"] = e2e
         if not args.no_extra:
             line["extra"] = _extras(torch, qs, stream, hbm_peak)
             line["batched"] = _batched(torch, qs, stream)
