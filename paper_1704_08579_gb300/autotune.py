@@ -51,6 +51,19 @@ def signature(kind: str, n: int, nseg: int) -> str:
     return "%s:n2^%d:seg2^%d" % (kind, max(n, 1).bit_length() - 1, max(nseg, 1).bit_length() - 1)
 
 
+def cached_entry(cache: dict, sig: str, kind: str):
+    """The cached choice for `sig`, or None when there is none or it names a
+    value outside the current candidate lists (a cache written by a library
+    whose tile variants or thresholds differed: the tile selector values
+    change with the compiled variants, so such an entry is tuned again)."""
+    e = cache.get(sig)
+    if not isinstance(e, dict):
+        return None
+    ok = (e.get("leaf_max") in LEAF_CHOICES[kind] and e.get("small_max") in SMALL_CHOICES
+          and e.get("driver_items") in ITEMS_CHOICES[kind])
+    return e if ok else None
+
+
 def apply(cfg: dict) -> None:
     qs.set_option("leaf_max", int(cfg.get("leaf_max", 0)))
     qs.set_option("small_max", int(cfg.get("small_max", 0)))
@@ -69,9 +82,10 @@ def tune(keys, offsets=None, values=None, reps: int = 2, use_cache: bool = True,
     gpu = torch.cuda.get_device_name()
     sig = signature(kind, keys.numel(), nseg)
     cache = _load_cache(gpu) if use_cache else {}
-    if use_cache and sig in cache:
-        apply(cache[sig])
-        return dict(cache[sig], cached=True)
+    hit = cached_entry(cache, sig, kind) if use_cache else None
+    if hit is not None:
+        apply(hit)
+        return dict(hit, cached=True)
     stream = stream or torch.cuda.current_stream()
     work_k = torch.empty_like(keys)
     work_v = torch.empty_like(values) if values is not None else None
@@ -99,7 +113,7 @@ def tune(keys, offsets=None, values=None, reps: int = 2, use_cache: bool = True,
         table.append(row)
         return row
 
-    # Thresholds with the wide tile, then the tile variants at the best thresholds.
+    # Thresholds with the kind's default sort tile, then the other tile variants at the best thresholds.
     for leaf in LEAF_CHOICES[kind]:
         for small in SMALL_CHOICES:
             if small <= leaf:
