@@ -65,7 +65,9 @@ typedef enum {
     QS_ERR_CUDA = -4,        /* a CUDA runtime call failed */
     QS_ERR_TIMEOUT = -5,     /* a device-side bounded wait ran out */
     QS_ERR_CAPACITY = -6,    /* task / look-back / leaf capacity exceeded on the device */
-    QS_ERR_INTERNAL = -7     /* recursion deeper than the supported limit */
+    QS_ERR_INTERNAL = -7     /* recursion deeper than the supported limit, or an internal
+                                consistency check failed (an index that would have been
+                                out of range: nothing was written there) */
 } qs_status;
 
 typedef enum { QS_KIND_I32 = 0, QS_KIND_F64 = 1, QS_KIND_KV = 2 } qs_kind;
