@@ -147,6 +147,8 @@ int qs_sort_segmented_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, const int6
  * every bucket first (its 255 splitters sampled from the bucket itself:
  * 1024 keys, every 4th of them sorted), and step 4 sorts the 65,536
  * sub-buckets -- most of them small enough for the leaf kernel alone.
+ * Step 4's partition passes use the kind's first compiled tile (int32: the
+ * register tile; FP64: the wide prefetched tile), not QS_OPT_DRIVER_ITEMS.
  * The sorted output is the same as qs_sort_*'s (keys bit for bit).
  *
  * d_params: device float array of qs_mlp_param_count() parameters laid out as
@@ -213,7 +215,8 @@ int qs_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, in
  * kernel writes each sorted part straight into them, so the return transfer
  * overlaps the leaf sorts; otherwise the result is copied back afterwards.
  * Synchronous: returns once the host buffers hold the result, QS_OK or a
- * negative qs_status.
+ * negative qs_status.  Host-buffer sorts on one device share its staging
+ * area: calls from several host threads run one after another.
  */
 int qs_sort_host_i32(int32_t *h_keys, int64_t n, qs_stream_t stream);
 int qs_sort_host_f64(double *h_keys, int64_t n, qs_stream_t stream);

@@ -54,6 +54,7 @@ int cuda_fail(cudaError_t e, const char *what)
 
 struct Workspace {
     std::mutex mu;
+    std::mutex host_mu;  // host-buffer sorts: one at a time (they share the staging area)
     bool init = false;
     int sms = 0;
     int occ[3][4] = {};  // per kind: driver (wide tile), leaf, driver (narrow tile), driver (register tile)
@@ -618,6 +619,9 @@ int run_host(int kind, K *h_keys, int32_t *h_vals, int64_t n, qs_stream_t stream
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(QS_ERR_INVALID_ARG, "device %d out of range", dev);
     Workspace &w = *workspace_for(dev);
+    // Held for the whole call: the staging area is filled, sorted and read
+    // back before another host-buffer sort on this device may touch it.
+    std::lock_guard<std::mutex> host_guard(w.host_mu);
     K *dk = nullptr;
     int32_t *dv = nullptr;
     {
@@ -760,9 +764,10 @@ int run_learned(int kind, K *keys, int64_t n, int op, const float *params, const
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.stream = s;
     const int64_t ctas = g_driver_ctas.load();
-    cfg.items = static_cast<int>(g_driver_items.load());
-    if (cfg.items == 0) cfg.items = limits_of(kind).items_default;
-    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][tile_variant(kind, cfg.items)];
+    // The bucket forms' final segmented sort runs the kind's first compiled
+    // partition tile (occupancy slot 0) whatever QS_OPT_DRIVER_ITEMS says.
+    cfg.items = limits_of(kind).items_wide;
+    cfg.grid_driver = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][0];
     cfg.grid_leaf = ctas > 0 ? static_cast<int>(ctas) : w.sms * w.occ[kind][1];
     cfg.profile = g_profile.load();
     for (int i = 0; i < 6; ++i) cfg.ev[i] = w.ev[i];
