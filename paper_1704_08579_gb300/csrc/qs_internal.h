@@ -28,7 +28,7 @@ namespace qs {
 
 constexpr int kThreads = 256;            // threads per CTA in every kernel
 constexpr int kWarps = kThreads / 32;
-constexpr int kDThreads = 256;           // threads per CTA of the persistent partition kernel
+constexpr int kDThreads = 256;           // default threads per CTA of the persistent partition kernel (Traits::DT)
 constexpr int kLThreads = 1024;          // threads per CTA of the leaf kernel (one CTA per SM)
 constexpr int kDWarps = kDThreads / 32;
 
