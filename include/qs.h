@@ -135,8 +135,11 @@ int qs_sort_segmented_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, const int6
  *      to [0,1] (qs_sketch_*);
  *   2. an FP32 MLP 1024 -> 64 (ReLU) -> 64 (ReLU) -> 256 softplus increments,
  *      whose normalised cumulative sums give 255 monotone positions q in
- *      [0,1] along the sorted sample; splitter j interpolates linearly between
- *      the sample keys around position q_j * 1023 (rounded for int32);
+ *      [0,1] along the sorted sample; splitter j is read at position
+ *      q_j * 1023 of the sample's curve -- the sorted sample smoothed by a
+ *      centred moving average of 17 keys (the window shrinking at both ends)
+ *      -- by linear interpolation between neighbouring curve points (rounded
+ *      for int32);
  *   3. a 256-way bucket pass: bucket(k) = number of splitters <= k
  *      (qs_bucket_* runs it alone, with the caller's splitters);
  *   4. the plain method on every bucket (the segmented sort).  A bucket that
