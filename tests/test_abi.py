@@ -3,6 +3,7 @@ point that include/qs.h declares, and its host-side argument checks return the
 documented status codes.  No call here reaches a kernel."""
 import ctypes
 import os
+import re
 
 import pytest
 
@@ -96,6 +97,13 @@ def test_host_argument_checks(lib):
     assert b"null" in lib.qs_last_error()
     assert lib.qs_sort_f64(ctypes.c_void_p(4), 10, null) == -2  # misaligned double pointer
     assert lib.qs_reserve(10, 7) == -1
+    # The no-allocation partition checks its arguments before any CUDA call.
+    cap = 1 << int(re.search(r"#define QS_NOALLOC_MAX_N \(1 << (\d+)\)", open(qs.HEADER).read()).group(1))
+    assert lib.qs_partition_i32_noalloc(null, 0, 5, null) == 0
+    assert lib.qs_partition_i32_noalloc(null, cap + 1, 5, null) == -1
+    assert lib.qs_partition_i32_noalloc(null, -1, 5, null) == -1
+    assert lib.qs_partition_i32_noalloc(null, 10, 5, null) == -1
+    assert lib.qs_partition_i32_noalloc(ctypes.c_void_p(6), 10, 5, null) == -2
     st = qs.stats()
     assert set(st) >= {"part_tasks", "part_keys", "leaf_keys", "ms_driver"}
 
