@@ -83,3 +83,32 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("LOCAL_RANK", "1")
     assert bench.run_reference(argparse.Namespace(steps=1, warmup=3)) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank_zero(monkeypatch, capsys):
+    """Rank 0 prints one JSON line with the contract's keys: the oracle's
+    throughput on its bounded sample, the same figure as its cpu_baseline and
+    as its end-to-end value (no host-device copies)."""
+    import json
+    import sys
+
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    # main() formats these module globals; restore them afterwards.
+    monkeypatch.setattr(bench, "WORKLOAD", bench.WORKLOAD)
+    monkeypatch.setattr(bench, "N_KEYS", bench.N_KEYS)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert bench.main() == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["higher_is_better"] is True and d["dtype"] == "f64" and d["value"] > 0
+    assert d["config"]["workload"].startswith("f64 sort, n=2^28") and d["config"]["n"] == 1 << 28
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["nproc"] >= 1 and "cpu_model" in cb
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
