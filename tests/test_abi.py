@@ -136,3 +136,22 @@ def test_stats_layout_matches_header(tmp_path):
     assert int(out["size"]) == ctypes.sizeof(qs.Stats)
     for f in fields:
         assert int(out[f]) == getattr(qs.Stats, f).offset, f
+
+
+def test_no_cpu_fallback(monkeypatch):
+    """CPU tensors are refused (nothing sorts them on the host), and without
+    the built library every call raises instead of running anything else."""
+    torch = pytest.importorskip("torch")
+    x = torch.arange(10, 0, -1, dtype=torch.int32)
+    before = x.clone()
+    with pytest.raises(ValueError):
+        qs.sort(x)
+    with pytest.raises(ValueError):
+        qs.partition(x, 5)
+    assert torch.equal(x, before)
+    monkeypatch.setattr(qs, "_lib", None)
+    monkeypatch.setattr(qs, "LIB_PATH", os.path.join(os.path.dirname(qs.LIB_PATH), "missing", "libqs.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        qs.load()
+    with pytest.raises(RuntimeError, match="not built"):
+        qs.sort(x)
