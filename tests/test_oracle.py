@@ -103,7 +103,7 @@ def _expected_partition(x, pivot):
     return len(low), low + high[::-1]
 
 
-@pytest.mark.parametrize("n", range(0, 7))
+@pytest.mark.parametrize("n", range(0, 9))
 def test_partition_brute_force(n):
     for perm in itertools.permutations(range(n)):
         x = np.array(perm, dtype=np.int32)
@@ -112,6 +112,24 @@ def test_partition_brute_force(n):
             exp_split, exp = _expected_partition(perm, pivot)
             assert split == exp_split == sum(1 for a in perm if a < pivot)
             assert out.tolist() == exp
+
+
+@pytest.mark.parametrize("n", range(0, 8))
+def test_partition_kv_brute_force_with_duplicates(n):
+    """Every key sequence over {0, 1, 2} with value = original index, every
+    pivot: the values name exactly which element went where, so the canonical
+    order among equal keys (lower side in input order, upper side in reverse
+    input order) is pinned, not only the keys."""
+    idx = np.arange(n, dtype=np.int32)
+    for seq in itertools.product(range(3), repeat=n):
+        k = np.array(seq, dtype=np.int32)
+        for pivot in range(-1, 4):
+            split, ko, vo = oracle.partition(k, pivot, idx)
+            low = [i for i in range(n) if seq[i] < pivot]
+            high = [i for i in range(n) if not seq[i] < pivot][::-1]
+            assert split == len(low)
+            assert vo.tolist() == low + high
+            assert ko.tolist() == [seq[i] for i in low + high]
 
 
 @pytest.mark.parametrize("dtype", [np.int32, np.float64])
