@@ -77,6 +77,25 @@ def test_sort_i32_uniform_and_duplicates():
         np.testing.assert_array_equal(oracle.sort(x), np.sort(x, kind="stable"))
 
 
+def test_sort_f64_extremes():
+    """Infinities, the largest and smallest normals, subnormals and zero among
+    ordinary keys (no NaN, no -0.0: the inputs' precondition) sort as numpy
+    sorts them, bit for bit; so do mixed int32 extremes."""
+    tiny = np.finfo(np.float64).tiny
+    special = np.array([np.inf, -np.inf, np.finfo(np.float64).max, -np.finfo(np.float64).max, tiny, -tiny,
+                        5e-324, -5e-324, tiny / 3, 0.0, 1.0, -1.0], dtype=np.float64)
+    rng = np.random.default_rng(5)
+    for reps in (1, 7, 300):
+        x = np.concatenate([np.repeat(special, reps), synth.uniform_f64(1000, 31)])
+        x = x[rng.permutation(x.size)]
+        got = oracle.sort(x)
+        assert np.array_equal(got.view(np.int64), np.sort(x, kind="stable").view(np.int64))
+    e = np.array([-2**31, 2**31 - 1, 0, -1, 1], dtype=np.int32)
+    y = np.concatenate([np.repeat(e, 101), synth.uniform_i32(999, 32)])
+    y = y[rng.permutation(y.size)]
+    np.testing.assert_array_equal(oracle.sort(y), np.sort(y, kind="stable"))
+
+
 @pytest.mark.parametrize("dist", ["uniform", "mod1000", "sorted", "reverse"])
 def test_sort_kv_values_follow_keys(dist):
     k, v = synth.kv_config(dist, 1 << 15)
