@@ -233,7 +233,7 @@ int qs_sort_host_kv(int32_t *h_keys, int32_t *h_vals, int64_t n, qs_stream_t str
  * caller working inside a fixed device-memory budget owned by its own
  * allocator, or one that must never cause that implicit synchronisation,
  * cannot let them.  This variant allocates nothing: its scratch is one fixed
- * file-scope device array of about 4.2 MiB that every GPU loading the library
+ * file-scope device array of 4,208,128 bytes (4.0 MiB) that every GPU loading the library
  * holds until the process exits.
  *   - Same operation, arguments, result order, return value and wait limit
  *     (QS_OPT_WAIT_LIMIT_NS) as qs_partition_i32, for 0 <= n <=
