@@ -305,7 +305,7 @@ const char *status_text(int s)
     switch (s) {
     case QS_ERR_TIMEOUT: return "a device-side wait ran out (QS_OPT_WAIT_LIMIT_NS)";
     case QS_ERR_CAPACITY: return "device task/look-back/leaf capacity exceeded";
-    case QS_ERR_INTERNAL: return "recursion deeper than the supported limit";
+    case QS_ERR_INTERNAL: return "recursion deeper than the supported limit, or a device index check failed";
     default: return "device error";
     }
 }
