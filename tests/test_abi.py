@@ -155,3 +155,42 @@ def test_no_cpu_fallback(monkeypatch):
         qs.load()
     with pytest.raises(RuntimeError, match="not built"):
         qs.sort(x)
+
+
+def test_plain_c_caller(tmp_path, lib):
+    """The boundary is usable from C alone: a program compiled with gcc against
+    include/qs.h and linked with libqs.so calls the entry points that return
+    before any CUDA call (version, options, argument checks, last error)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "caller.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "qs.h"
+int main(void) {
+    int64_t v = -1;
+    if (qs_version() < 100) return 1;
+    if (qs_set_option(QS_OPT_SYNC, 1) != QS_OK) return 2;
+    if (qs_get_option(QS_OPT_SYNC, &v) != QS_OK || v != 1) return 3;
+    if (qs_set_option(QS_OPT_SYNC, 0) != QS_OK) return 4;
+    if (qs_sort_i32(NULL, -1, NULL) != QS_ERR_INVALID_ARG) return 5;
+    if (strstr(qs_last_error(), "out of range") == NULL) return 6;
+    if (qs_sort_f64((double *)8, 0, NULL) != QS_OK) return 7;
+    if (qs_partition_kv(NULL, NULL, 0, 0, NULL) != 0) return 8;
+    if (qs_sort_f64((double *)4, 10, NULL) != QS_ERR_ALIGN) return 9;
+    if (qs_partition_i32_noalloc(NULL, QS_NOALLOC_MAX_N + 1, 0, NULL) != QS_ERR_INVALID_ARG) return 10;
+    printf("ok\n");
+    return 0;
+}
+""")
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(qs.LIB_PATH)
+    subprocess.run([cc, "-I", os.path.dirname(qs.HEADER), str(src), "-o", str(exe), "-L", libdir, "-lqs",
+                    "-Wl,-rpath," + libdir], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
