@@ -285,6 +285,7 @@ def _secondary(torch, qs, stream, name, make, steps=3, kind="f64"):
     bk = [dk.clone() for _ in range(steps + 1)]
     bv = [dv.clone() for _ in range(steps + 1)] if dv is not None else None
     del dk, dv
+    torch.cuda.synchronize()  # the copies (current stream) land before the sorts (`stream`) read them
     _time_sorts(torch, qs, bk[:1], stream, None if bv is None else bv[:1])  # warm-up
     ms, st = _time_sorts(torch, qs, bk[1:], stream, None if bv is None else bv[1:])
     b = keys.itemsize + (4 if vals is not None else 0)
@@ -325,6 +326,7 @@ def run_ours(args):
     total = args.warmup + args.steps
     bufs = [pristine.clone() for _ in range(total)]
     stream = torch.cuda.Stream()
+    torch.cuda.synchronize()  # the copies (current stream) land before the sorts (`stream`) read them
     qs.reserve(N_KEYS, "f64")
     # Timed steps record CUDA events around the kernels only; the in-kernel
     # cycle counters (profile level 2) run on one extra, untimed sort below.
@@ -447,6 +449,7 @@ def _batched(torch, qs, stream, nseg=20_000, steps=3):
         tuned = autotune.tune(dk, doffs, dv, reps=1, use_cache=False, stream=stream)
         bk = [dk.clone() for _ in range(steps)]
         bv = [dv.clone() for _ in range(steps)] if dv is not None else None
+        torch.cuda.synchronize()  # the copies land before the timed sorts on `stream` read them
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         with torch.cuda.stream(stream):
@@ -621,6 +624,7 @@ def _extras(torch, qs, stream, hbm_peak):
     d = torch.from_numpy(x).to("cuda")
     bufs = [d.clone() for _ in range(4)]
     del d
+    torch.cuda.synchronize()  # the copies land before the partitions on `stream` read them
     ms_k, ms_t, split = [], [], None
     with torch.cuda.stream(stream):
         for i, b in enumerate(bufs):

@@ -87,6 +87,8 @@ def tune(keys, offsets=None, values=None, reps: int = 2, use_cache: bool = True,
         apply(hit)
         return dict(hit, cached=True)
     stream = stream or torch.cuda.current_stream()
+    # The inputs were written on the caller's current stream: order `stream` after them.
+    stream.wait_stream(torch.cuda.current_stream())
     work_k = torch.empty_like(keys)
     work_v = torch.empty_like(values) if values is not None else None
     table = []
@@ -95,12 +97,14 @@ def tune(keys, offsets=None, values=None, reps: int = 2, use_cache: bool = True,
         apply(cfg)
         times = []
         for _ in range(reps + 1):  # the first run warms up (and captures the graph)
-            work_k.copy_(keys)
-            if work_v is not None:
-                work_v.copy_(values)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(stream):
+                # The fresh copy goes on the sort's own stream, so the sort
+                # starts only once its input has landed.
+                work_k.copy_(keys)
+                if work_v is not None:
+                    work_v.copy_(values)
                 a.record(stream)
                 if offsets is None:
                     qs.sort(work_k, work_v, stream=stream)
