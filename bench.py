@@ -352,7 +352,10 @@ def run_ours(args):
     del bufs
     torch.cuda.empty_cache()
     qs.set_option("profile", 2)
-    _, st_cycles = _time_sorts(torch, qs, [pristine.clone()], stream)
+    extra_buf = pristine.clone()
+    torch.cuda.synchronize()
+    _, st_cycles = _time_sorts(torch, qs, [extra_buf], stream)
+    del extra_buf
     qs.set_option("profile", 1)
     torch.cuda.empty_cache()
 
