@@ -188,6 +188,16 @@ def test_select():
     assert oracle.select(y, 2048) == sorted(y.tolist())[2048]
 
 
+def test_splitmix64_known_outputs():
+    """The generator both sides share is SplitMix64 as published (Steele, Lea
+    and Flood 2014; the reference C version by Vigna): seeded with 0, its first
+    outputs are these well-known values."""
+    got = [int(v) for v in synth.splitmix64(0, 0, 4)]
+    assert got == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    # counter based: output i does not depend on where the slice starts
+    assert [int(v) for v in synth.splitmix64(0, 2, 2)] == got[2:]
+
+
 def test_synth_properties():
     a = synth.uniform_f64(1 << 16, 1)
     assert np.all(np.isfinite(a)) and not np.any(np.signbit(a) & (a == 0))
