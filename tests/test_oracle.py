@@ -218,6 +218,30 @@ def test_synth_properties():
     assert offs[0] == 0 and offs[-1] == keys.size and np.all(np.diff(offs) >= 16)
 
 
+def test_skewed_workload_recipes():
+    """The learned-splitter and batched workloads follow their stated laws:
+    Zipf(1.2) over 2^24 values (the top value's share is 1 / sum k^-1.2, keys
+    on the grid k*256 - 2^31), lognormal(0, 2) (log x / 2 is standard normal),
+    an 8-Gaussian mixture inside the int32 range, and log-uniform segment sizes
+    in [16, 2^18)."""
+    n = 1 << 18
+    z = synth.zipf_i32(n, 41)
+    assert np.all((z.astype(np.int64) + 2**31) % 256 == 0)
+    top = np.bincount(((z.astype(np.int64) + 2**31) // 256).astype(np.int64)).max() / n
+    h = float(np.sum(np.arange(1, (1 << 24) + 1, dtype=np.float64) ** -1.2))
+    assert abs(top - 1 / h) < 0.01
+    lg = np.log(synth.lognormal_f64(n, 42)) / 2.0
+    assert abs(lg.mean()) < 0.01 and abs(lg.std() - 1.0) < 0.01
+    means, sig, cw = synth.gauss_mix_params(43)
+    g = synth.gauss_mix_i32(n, 43).astype(np.float64)
+    near = np.min(np.abs(g[:, None] - means[None, :]) / sig[None, :], axis=1)
+    assert means.size == 8 and np.all(np.diff(cw) > 0) and abs(cw[-1] - 1) < 1e-12
+    assert np.mean(near < 5) > 0.999
+    sizes = synth.segment_sizes(20000, 44)
+    assert sizes.min() >= 16 and sizes.max() < 1 << 18
+    assert abs(np.log(sizes + 0.5).mean() - (np.log(16) + np.log(1 << 18)) / 2) < 0.05
+
+
 @pytest.mark.parametrize("threads", [1, 2, 3, 16])
 def test_parallel_oracle_equals_sequential(threads):
     """The task-parallel oracle runs the same Appendix A steps: identical output."""
