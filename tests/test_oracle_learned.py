@@ -114,3 +114,19 @@ def test_adam_first_step_closed_form():
     # a second step with the same gradient keeps moving the same way
     p2, _, _ = oracle.adam_step(p1, g, m1, v1, 2, 0.01)
     assert np.all(np.sign(p1 - p2) == np.sign(g))
+
+
+def test_adam_constant_gradient_closed_form():
+    """With the same gradient at every step, the bias-corrected moments equal
+    g and g^2 exactly, so every step moves each parameter by lr * g / (|g| +
+    eps) -- a wrong bias-correction power or a swapped beta shows up by step 2."""
+    rng = np.random.default_rng(15)
+    p0 = rng.normal(size=500)
+    g = rng.normal(size=500)
+    p, m, v = p0.copy(), np.zeros(500), np.zeros(500)
+    step = 0.003 * g / (np.abs(g) + 1e-8)
+    for t in range(1, 9):
+        p, m, v = oracle.adam_step(p, g, m, v, t, 0.003)
+        np.testing.assert_allclose(p, p0 - t * step, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(m, (1 - 0.9 ** t) * g, rtol=1e-12)
+        np.testing.assert_allclose(v, (1 - 0.999 ** t) * g * g, rtol=1e-9)
