@@ -218,9 +218,20 @@ def cpu_oracle_baseline(sample_log2: int = 24, repeats: int = 3, seed: int | Non
         oracle.sort_inplace(y)
         times.append(time.perf_counter() - t0)
     t = statistics.median(times)
+    # Context beside it: the task-parallel form of the same oracle (identical
+    # output) on every host core, same sample.
+    threads = os.cpu_count() or 1
+    ptimes = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        oracle.sort_parallel(x, threads=threads)
+        ptimes.append(time.perf_counter() - t0)
+    tp = statistics.median(ptimes)
     return dict({"value": n / t / 1e9, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
                  "sample": "first 2^%d keys of the same seeded f64 stream, oracle quicksort, median of %d runs "
-                           "(%.2f s each)" % (sample_log2, repeats, t)}, **host_identity())
+                           "(%.2f s each)" % (sample_log2, repeats, t),
+                 "all_cores": {"value": n / tp / 1e9, "unit": "Gkeys/s", "cores": threads,
+                               "kind": "task-parallel oracle (same steps, same output)"}}, **host_identity())
 
 
 def run_reference(args):
