@@ -194,3 +194,18 @@ int main(void) {
                     "-Wl,-rpath," + libdir], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++11")])
+def test_header_is_clean_c_and_cxx(tmp_path, lang, std):
+    """include/qs.h compiles on its own as strict C99 and C++11, warnings as errors."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no compiler")
+    src = tmp_path / "hdr.c"
+    src.write_text('#include "qs.h"\nint main(void) { return QS_OK; }\n')
+    subprocess.run([cc, std, "-x", lang, "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.dirname(qs.HEADER),
+                    str(src), "-o", str(tmp_path / "hdr")], check=True)
