@@ -84,8 +84,9 @@ typedef enum { QS_KIND_I32 = 0, QS_KIND_F64 = 1, QS_KIND_KV = 2 } qs_kind;
  * earlier one has already read), the upper side into the workspace scratch,
  * from where it is copied back into d_keys/d_vals once the split is known
  * (2 * n + 2 * (n - split) element moves in all).  Returns a negative
- * qs_status on error; after a device-side failure the contents of
- * d_keys/d_vals are unspecified (keys may be duplicated or lost).
+ * qs_status on error (QS_ERR_INVALID_ARG for a NaN pivot, before any work);
+ * after a device-side failure the contents of d_keys/d_vals are unspecified
+ * (keys may be duplicated or lost).
  */
 int64_t qs_partition_i32(int32_t *d_keys, int64_t n, int32_t pivot, qs_stream_t stream);
 int64_t qs_partition_f64(double *d_keys, int64_t n, double pivot, qs_stream_t stream);

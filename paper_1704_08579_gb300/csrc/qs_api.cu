@@ -840,6 +840,8 @@ int64_t qs_partition_i32(int32_t *d_keys, int64_t n, int32_t pivot, qs_stream_t 
 
 int64_t qs_partition_f64(double *d_keys, int64_t n, double pivot, qs_stream_t stream)
 {
+    // Under IEEE '<' no key is below a NaN pivot, but no key is at-or-above it either.
+    if (pivot != pivot) return fail(QS_ERR_INVALID_ARG, "NaN pivot");
     return run<double>(QS_KIND_F64, d_keys, nullptr, n, bits_f64(pivot), 1, stream);
 }
 

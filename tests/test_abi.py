@@ -96,6 +96,8 @@ def test_host_argument_checks(lib):
     assert lib.qs_sort_i32(null, 10, null) == -1        # null pointer with n > 0
     assert b"null" in lib.qs_last_error()
     assert lib.qs_sort_f64(ctypes.c_void_p(4), 10, null) == -2  # misaligned double pointer
+    assert lib.qs_partition_f64(null, 10, float("nan"), null) == -1  # no side is defined for a NaN pivot
+    assert b"NaN" in lib.qs_last_error()
     assert lib.qs_reserve(10, 7) == -1
     # The no-allocation partition checks its arguments before any CUDA call.
     cap = 1 << int(re.search(r"#define QS_NOALLOC_MAX_N \(1 << (\d+)\)", open(qs.HEADER).read()).group(1))
