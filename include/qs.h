@@ -157,9 +157,12 @@ int qs_sort_segmented_kv(int32_t *d_keys, int32_t *d_vals, int64_t n, const int6
  *
  * d_params: device float array of qs_mlp_param_count() parameters laid out as
  * W1 (64x1024, row-major), b1 (64), W2 (64x64), b2 (64), W3 (256x64), b3
- * (256); NULL = sampled splitters (every 4th key of the sorted sketch sample),
- * the same bucket machinery without the model.  Arrays below 2^16 keys use the
- * plain method.  Synchronous; returns QS_OK or a negative qs_status.
+ * (256), all finite (not checked); NULL = sampled splitters (every 4th key of
+ * the sorted sketch sample), the same bucket machinery without the model.
+ * Whatever finite parameters give, the sorted output is the same: a key's
+ * bucket never decreases as the key grows, for any set of splitters.  Arrays
+ * below 2^16 keys use the plain method.  Synchronous; returns QS_OK or a
+ * negative qs_status.
  */
 int qs_sort_learned_i32(int32_t *d_keys, int64_t n, const float *d_params, qs_stream_t stream);
 int qs_sort_learned_f64(double *d_keys, int64_t n, const float *d_params, qs_stream_t stream);
