@@ -1,6 +1,9 @@
 """qs_partition_i32_noalloc, the partition for callers that cannot let the
-library allocate device memory (its scratch is one fixed device array instead
-of the growable workspace).  Its split index and every output element must
+library allocate device memory: code that works inside a fixed device-memory
+budget handed out by its own allocator, or that must never be stalled by the
+device-wide synchronisation of cudaFree with which the regular workspace is
+resized.  Its scratch is one fixed device array instead of the growable
+workspace.  Its split index and every output element must
 equal the oracle's partition (Section III-B, with the lower side in input
 order and the upper side in reverse input order), exactly as
 qs_partition_i32's do.  This file is collected last so that a run stopping at
@@ -82,18 +85,21 @@ def test_noalloc_unaligned_pointer(koff):
 
 
 def test_noalloc_agrees_with_regular_entry_point():
+    """Two calls in a row, each against qs_partition_i32 on the same input:
+    the same split and the same keys in the same order."""
     import torch
 
     qs = qs_gpu()
     lib = qs.load()
-    x = synth.uniform_i32(250_001, 930)
-    pivot = int(x[11])
-    ref = to_dev(x)
-    split_ref = lib.qs_partition_i32(ctypes.c_void_p(ref.data_ptr()), x.size, pivot, _stream())
-    split, got = _noalloc(lib, x, pivot, _stream())
-    torch.cuda.synchronize()
-    assert split == split_ref
-    assert_keys_equal(got, ref.cpu().numpy())
+    for n, seed in ((250_001, 930), (MAX_N, 931)):
+        x = synth.uniform_i32(n, seed)
+        pivot = int(x[11])
+        ref = to_dev(x)
+        split_ref = lib.qs_partition_i32(ctypes.c_void_p(ref.data_ptr()), x.size, pivot, _stream())
+        split, got = _noalloc(lib, x, pivot, _stream())
+        torch.cuda.synchronize()
+        assert split == split_ref
+        assert_keys_equal(got, ref.cpu().numpy())
 
 
 def test_noalloc_honours_the_wait_limit_and_recovers():
